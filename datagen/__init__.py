@@ -1,0 +1,157 @@
+"""Seeded synthetic inputs for MAPI workloads.
+
+This module is the one piece of code that both the CPU oracle (``oracle/``)
+and the CUDA path use.  It holds none of the method's arithmetic: it draws
+matrices, data sets, graphs and start vectors with numpy's PCG64 generator and
+returns them.  Every MAVP product, normalisation, covariance, deflation and
+Google-matrix step lives on each side separately.
+
+Workload shapes follow the paper's experiments:
+
+* a dense symmetric Gaussian matrix for plain MAPI / RPI (Alg. 1);
+* zero-mean D x N data with a few strong principal directions and impulsive
+  outliers, the setting of the min-covariance PCA experiments (§3.1: image
+  patches with occluding noise; §2.1 Eq. (5));
+* a directed scale-free graph for PageRank (§3.3, Eq. (11)); the paper's
+  Gnutella graphs are not available, so a Barabasi-Albert digraph of the same
+  kind (power-law in-degree) stands in for them;
+* symmetric positive semi-definite Wishart instances of mixed sizes for
+  batched runs;
+* start vectors drawn uniformly (Alg. 1 step 1 asks for a random w0).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "rng",
+    "start_vector",
+    "start_vectors",
+    "symmetric_gaussian",
+    "spiked_pca_data",
+    "barabasi_albert_digraph",
+    "wishart_sizes",
+    "wishart_instance",
+    "small_grid_matrix",
+]
+
+DEFAULT_SPIKES = (50.0, 30.0, 20.0, 10.0, 5.0, 4.0, 3.0, 2.0)
+
+
+def rng(seed: int) -> np.random.Generator:
+    """numpy Generator over PCG64 with the given seed."""
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def start_vector(n: int, seed: int, low: float = -1.0, high: float = 1.0,
+                 dtype=np.float32) -> np.ndarray:
+    """Uniform(low, high)^n draw, cast to ``dtype`` (raw, not normalised)."""
+    return rng(seed).uniform(low, high, size=n).astype(dtype)
+
+
+def start_vectors(n: int, k: int, seed: int, low: float = -1.0,
+                  high: float = 1.0, dtype=np.float32) -> np.ndarray:
+    """k uniform start vectors as an n x k column-major (Fortran) array."""
+    v = rng(seed).uniform(low, high, size=(k, n)).astype(dtype)
+    return np.asfortranarray(v.T)
+
+
+def symmetric_gaussian(n: int, seed: int = 0, dtype=np.float64) -> np.ndarray:
+    """A = (G + G^T)/2 with G_ij ~ N(0, 1): a dense symmetric test matrix."""
+    g = rng(seed).standard_normal((n, n))
+    return ((g + g.T) * 0.5).astype(dtype)
+
+
+def spiked_pca_data(D: int, N: int, seed: int = 0,
+                    spikes=DEFAULT_SPIKES, outlier_frac: float = 0.01,
+                    laplace_scale: float = 20.0,
+                    dtype=np.float32, chunk: int = 8192) -> np.ndarray:
+    """Zero-mean D x N data (row-major) with a spiked covariance and outliers.
+
+    Column x = U diag(sqrt(lambda - 1)) z_k + z_D, where U (D x k) is a random
+    orthonormal basis (QR of a Gaussian matrix) and z ~ N(0, I), so the
+    population covariance has eigenvalues ``spikes`` and 1 elsewhere.  Then a
+    fraction ``outlier_frac`` of the entries (a seeded mask) is replaced by
+    Laplace(0, laplace_scale) draws, the impulsive noise the min-covariance is
+    meant to resist, and finally every row's mean is removed so that the data
+    set is zero-mean as the PCA setting of §1 requires.
+    """
+    r = rng(seed)
+    k = min(len(spikes), D)
+    lam = np.asarray(spikes[:k], dtype=np.float64)
+    q, _ = np.linalg.qr(r.standard_normal((D, k)))
+    scale = np.sqrt(np.maximum(lam - 1.0, 0.0))
+    X = np.empty((D, N), dtype=np.float64)
+    for c0 in range(0, N, chunk):
+        c1 = min(N, c0 + chunk)
+        z_k = r.standard_normal((k, c1 - c0))
+        z_d = r.standard_normal((D, c1 - c0))
+        X[:, c0:c1] = q @ (scale[:, None] * z_k) + z_d
+    mask = r.random((D, N)) < outlier_frac
+    cnt = int(mask.sum())
+    X[mask] = r.laplace(0.0, laplace_scale, size=cnt)
+    X -= X.mean(axis=1, keepdims=True)
+    return np.ascontiguousarray(X.astype(dtype))
+
+
+def barabasi_albert_digraph(n: int, m: int = 8, seed: int = 0):
+    """Directed preferential-attachment graph as out-link CSR (indptr, indices).
+
+    The first ``m`` nodes start isolated (they have no out-links, i.e. they are
+    dangling).  Every later node v links to ``m`` distinct earlier nodes, each
+    picked with probability proportional to (in-degree + out-degree + 1).
+    Returns int32 arrays: the out-neighbours of node j are
+    ``indices[indptr[j]:indptr[j+1]]`` (sorted ascending).
+    """
+    r = rng(seed)
+    # urn holds every node once (the "+1") plus once per incident edge end
+    urn = list(range(min(m, n)))
+    out = [[] for _ in range(n)]
+    for v in range(m, n):
+        chosen = set()
+        while len(chosen) < m:
+            # draw in small batches to keep the Python loop short
+            picks = r.integers(0, len(urn), size=2 * m)
+            for p in picks:
+                t = urn[int(p)]
+                if t not in chosen:
+                    chosen.add(t)
+                    if len(chosen) == m:
+                        break
+        tgt = sorted(chosen)
+        out[v] = tgt
+        urn.extend(tgt)          # targets gain in-degree
+        urn.extend([v] * m)      # v gains out-degree
+        urn.append(v)            # v joins with weight 1
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    for j in range(n):
+        indptr[j + 1] = indptr[j] + len(out[j])
+    indices = np.fromiter((t for j in range(n) for t in out[j]),
+                          dtype=np.int32, count=int(indptr[-1]))
+    return indptr.astype(np.int32), indices
+
+
+def wishart_sizes(count: int, seed: int = 0, nmin: int = 64,
+                  nmax: int = 2048) -> np.ndarray:
+    """Instance sizes n = floor(exp(U(ln nmin, ln nmax))), int32."""
+    u = rng(seed).uniform(math.log(nmin), math.log(nmax), size=count)
+    return np.clip(np.floor(np.exp(u)), nmin, nmax).astype(np.int32)
+
+
+def wishart_instance(n: int, seed: int, dtype=np.float32) -> np.ndarray:
+    """A = W W^T / k with W ~ N(0,1)^{n x k}, k = max(1, n // 2)."""
+    k = max(1, n // 2)
+    w = rng(seed).standard_normal((n, k))
+    return ((w @ w.T) / k).astype(dtype)
+
+
+def small_grid_matrix(n: int, seed: int, grid=(-2, -1, 0, 1, 2, 3)) -> np.ndarray:
+    """n x n integer matrix with entries drawn from a small signed grid.
+
+    Small integers make exact rational brute force cheap and create ties and
+    zeros on purpose.
+    """
+    g = np.asarray(grid, dtype=np.int64)
+    return g[rng(seed).integers(0, len(g), size=(n, n))]
