@@ -1,0 +1,455 @@
+"""Benchmark of the MAPI hot path on GB300 (prints one JSON line).
+
+Workload (one step): MAPI-PCA top-8 principal vectors with deflation on a
+zero-mean X of D = 1024 by N = 65536 (spiked covariance 50, 30, 20, 10, 5, 4,
+3, 2 then 1, plus 1% Laplace(0, 20) outliers; seeded synthetic data), FP32
+storage, min1 product, 100 iterations per vector, matrix-free pair mode:
+pack X, then for each component 100 x (pair step over X, reduction, deflation,
+l1 normalisation), then the l2 step.  value = MAPI iterations per second over
+all ranks (800 per step per rank).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank solves its own seeded instance (weak scaling, no
+collective on the data path).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("MAPI iterations/s and matrix GB/s (% of HBM / ALU peak); "
+          "served p50/p99 latency vs plain")
+UNIT = "MAPI iterations/s"
+D, N, K_COMP, ITERS = 1024, 65536, 8, 100
+WORKLOAD = ("MAPI-PCA top-8 with deflation, pair mode, D=1024 x N=65536 spiked covariance "
+            "(50,30,20,10,5,4,3,2 then 1) + 1% Laplace(0,20) outliers, FP32 storage, min1, "
+            "100 iterations per vector")
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def source_digest(*names) -> str:
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2110_12065_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(summary: str, digest: str):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    summary is missing or was taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_digest") != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"].replace(",", ""))
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join("/tmp", f"mapi_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- GPU arm
+
+def make_inputs(rank: int):
+    import datagen
+    X = datagen.spiked_pca_data(D, N, seed=rank)
+    W0 = np.stack([datagen.start_vector(D, seed=1000 + 17 * rank + c) for c in range(K_COMP)])
+    return X, W0
+
+
+def run_gpu(args, rank, world, local_rank, dist):
+    import torch
+
+    import paper_2110_12065_gb300 as M
+    from paper_2110_12065_gb300 import build as B
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ctx = M.mapi_create(local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    X, W0 = make_inputs(rank)
+    Xd = torch.from_numpy(X).to(dev)
+    W0d = torch.from_numpy(W0).to(dev)
+    P = torch.empty_like(W0d)
+
+    def step(xsrc, storage="f32", mode="pair", op="min1"):
+        mat = M.mapi_matrix_upload(ctx, xsrc, storage)
+        try:
+            M.mapi_pca_topk(ctx, mat, K_COMP, mode, op, ITERS, float(N), W0d, P_out=P)
+        finally:
+            M.mapi_matrix_free(ctx, mat)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(Xd)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    M.mapi_profile(ctx, True)
+    M.mapi_get_stats(ctx, reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(Xd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    stats = M.mapi_get_stats(ctx, reset=True)
+    M.mapi_profile(ctx, False)
+    ms = e0.elapsed_time(e1)
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    iters = K_COMP * ITERS * args.steps
+    value = iters * world / (t_max / 1e3)
+    xbytes = D * N * 4
+
+    peaks = measured_peaks()
+    pair = stats["pair"]
+    achieved = (pair["bytes"] / pair["launches"]) / (pair["ms"] / pair["launches"] / 1e3) / 1e9
+    digest = source_digest("pca.cu", "device_common.cuh")
+    traffic = ncu_traffic("k_pair_partial_pca_d1024_n65536_f32.txt", digest)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "traffic": traffic, "kernel": "k_pair_partial (pair step over X)",
+                "peak_source": peaks["source"],
+                "algorithmic_bytes_per_launch": pair["bytes"] / pair["launches"],
+                "avg_launch_us": round(pair["ms"] / pair["launches"] * 1e3, 3),
+                "kernel_share_of_step": round(pair["ms"] / ms, 4)}
+
+    # ---- end to end: host (pinned) X -> library upload -> solve -> host P
+    Xh = torch.from_numpy(X).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    step(Xh)
+    P.cpu()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step(Xh)
+        _ = P.cpu()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(K_COMP * ITERS * e2e_steps * world / e2e_s, 1), "unit": UNIT,
+           "h2d_bytes_per_step": xbytes, "d2h_bytes_per_step": K_COMP * D * 4}
+
+    variants = {} if args.no_variants or rank != 0 else run_variants(M, ctx, torch, dev, X, W0d,
+                                                                   peaks)
+    torch.cuda.synchronize()
+    M.mapi_destroy(ctx)
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "D": D, "N": N, "k": K_COMP, "iters_per_vec": ITERS,
+                   "mode": "pair", "op": "min1", "storage": "f32", "parallelism":
+                   f"replicas x{world}",
+                   "l2": "inputs larger than L2 (X = 268 MB FP32 vs 126 MB L2)"},
+        "matrix_gbs": round(value / world * xbytes / 1e9 * world, 1),
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(stats["launches"]),
+        "clocks": clocks,
+        "variants": variants,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(X, W0, seconds=args.cpu_seconds)
+    return line
+
+
+def timed(torch, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_variants(M, ctx, torch, dev, X, W0d, peaks):
+    """Short measurements of the other workloads (not the headline)."""
+    import datagen
+    out = {}
+    Xd = torch.from_numpy(X).to(dev)
+    P = torch.empty_like(W0d)
+    hbm = peaks["hbm_gbs"]
+
+    def pca(storage, mode):
+        mat = M.mapi_matrix_upload(ctx, Xd, storage)
+        try:
+            M.mapi_get_stats(ctx, reset=True)
+            M.mapi_profile(ctx, True)
+            ms = timed(torch, lambda: M.mapi_pca_topk(ctx, mat, K_COMP, mode, "min1", ITERS,
+                                                      float(N), W0d, P_out=P), 1)
+            st = M.mapi_get_stats(ctx, reset=True)
+            M.mapi_profile(ctx, False)
+        finally:
+            M.mapi_matrix_free(ctx, mat)
+        return ms, st
+
+    ms, st = pca("bf16", "pair")
+    pr = st["pair"]
+    gbs = pr["bytes"] / (pr["ms"] / 1e3) / 1e9
+    out["pca_pair_bf16"] = {"iters_per_s": round(K_COMP * ITERS / (ms / 1e3), 1),
+                            "ms_per_solve": round(ms, 3), "pair_kernel_gbs": round(gbs, 1),
+                            "hbm_frac": round(gbs / hbm, 4)}
+    for stg in ("f32", "bf16"):
+        ms, st = pca(stg, "mincov")
+        mc, gv = st["mincov"], st["gemv"]
+        out[f"pca_mincov_{stg}"] = {
+            "ms_per_solve": round(ms, 3), "iters_per_s": round(K_COMP * ITERS / (ms / 1e3), 1),
+            "build_ms": round(mc["ms"] / max(1, mc["launches"]), 3),
+            "build_terms_per_s": round(mc["terms"] / (mc["ms"] / 1e3), 1) if mc["ms"] else None,
+            "iterate_us_per_step": round(gv["ms"] / max(1, gv["launches"]) * 1e3, 3)}
+
+    # plain MAPI / RPI on the n = 512 symmetric Gaussian, 200 steps
+    A = datagen.symmetric_gaussian(512, seed=0).astype(np.float32)
+    w0 = torch.from_numpy(datagen.start_vector(512, seed=0)).to(dev)
+    mat = M.mapi_matrix_upload(ctx, torch.from_numpy(A).to(dev), "f32")
+    for op in ("min1", "min2", "dot"):
+        ms = timed(torch, lambda: M.mapi_iterate(ctx, mat, op, w0, 200), 5)
+        out[f"plain_n512_{op}"] = {"iters_per_s": round(200 / (ms / 1e3), 1),
+                                   "us_per_iter": round(ms / 200 * 1e3, 3)}
+    M.mapi_matrix_free(ctx, mat)
+
+    # PageRank on a dense Google matrix, n = 16384, 100 steps per storage
+    n = 16384
+    ip, ix = datagen.barabasi_albert_digraph(n, m=8, seed=0)
+    dip, dix = torch.from_numpy(ip).to(dev), torch.from_numpy(ix).to(dev)
+    w0 = torch.from_numpy(datagen.start_vector(n, seed=0, low=0.0, high=1.0)).to(dev)
+    for stg in ("f32", "bf16", "fp8", "i16"):
+        G = M.mapi_google_matrix(ctx, dip, dix, n, 0.85, stg)
+        try:
+            M.mapi_get_stats(ctx, reset=True)
+            M.mapi_profile(ctx, True)
+            ms = timed(torch, lambda: M.mapi_iterate(ctx, G, "min1", w0, 100), 2)
+            st = M.mapi_get_stats(ctx, reset=True)
+            M.mapi_profile(ctx, False)
+        finally:
+            M.mapi_matrix_free(ctx, G)
+        gv = st["gemv"]
+        gbs = gv["bytes"] / (gv["ms"] / 1e3) / 1e9
+        out[f"pagerank_n16384_{stg}"] = {"iters_per_s": round(100 / (ms / 1e3), 1),
+                                         "gemv_gbs": round(gbs, 1),
+                                         "hbm_frac": round(gbs / hbm, 4)}
+    return out
+
+
+# --------------------------------------------------------------- CPU arm
+
+def cpu_baseline(X, W0, seconds: float = 10.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    pair steps of the second component (one earlier component to deflate) on
+    the full X, timed on the host cores."""
+    import oracle
+    Xf = np.ascontiguousarray(X, dtype=np.float64)
+    w = W0[1].astype(np.float64)
+    w /= np.linalg.norm(w)
+    prev = W0[0].astype(np.float64)
+    prev /= np.linalg.norm(prev)
+
+    def one():
+        nonlocal w
+        y = oracle.pair_step("min1", Xf, w, float(N))
+        y = oracle.deflate_vec("min1", y, prev[:, None])
+        w = y / np.abs(y).sum()
+
+    t0 = time.perf_counter()
+    one()
+    first = time.perf_counter() - t0
+    reps = max(1, int(seconds / max(first, 1e-3)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        one()
+    dt = time.perf_counter() - t0
+    return {"value": round(reps / dt, 4), "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"{reps} pair steps (component 2, one deflation) on the full "
+                      f"D=1024 x N=65536 X, FP64, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores, same metric."""
+    if rank != 0:
+        return None
+    X, W0 = make_inputs(0)
+    import oracle
+    per_step = 2
+    Xf = np.ascontiguousarray(X, dtype=np.float64)
+    w = W0[1].astype(np.float64)
+    w /= np.linalg.norm(w)
+    prev = W0[0].astype(np.float64)
+    prev /= np.linalg.norm(prev)
+
+    def step():
+        nonlocal w
+        for _ in range(per_step):
+            y = oracle.pair_step("min1", Xf, w, float(N))
+            y = oracle.deflate_vec("min1", y, prev[:, None])
+            w = y / np.abs(y).sum()
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "D": D, "N": N, "k": K_COMP, "iters_per_vec": ITERS,
+                   "mode": "pair", "op": "min1"},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": oracle.max_threads(),
+                         "kind": "oracle",
+                         "sample": f"{per_step} pair steps per step (component 2, one "
+                                   f"deflation) on the full X, FP64"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", rank=rank, world_size=world)
+        dist = tdist
+    line = run_gpu(args, rank, world, local_rank, dist)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,291 @@
+/*
+ * mapi.h -- C ABI of the GB300 (sm_103a) library for multiplication-avoiding
+ * power iteration (MAPI), after H. Pan, D. Badawi, R. Miao, E. Koyuncu and
+ * A. E. Cetin, "Multiplication-Avoiding Variant of Power Iteration with
+ * Applications" (arXiv 2110.12065).
+ *
+ * Vocabulary (paper notation)
+ *   (+)   an MAVP "vector product": min1 (.) of Eq. (3),
+ *         w^T (.) x = sum_i sign(w_i x_i) min(|w_i|, |x_i|), or min2 (.)_m of
+ *         Eq. (4), sum_i 1(sign w_i = sign x_i) min(|w_i|, |x_i|).
+ *   A (+) w   the row-wise product: (A (+) w)_i = a_i^T (+) w, a_i = row i.
+ *   MAPI  Eq. (6) / Alg. 1: w <- (A (+) w) / ||A (+) w||_1.
+ *   RPI   Eq. (1): b <- A b / ||A b||_2 (op MAPI_OP_DOT).
+ *
+ * Conventions for every entry point
+ *   - Every call returns a mapi_status; nothing throws across the ABI.
+ *   - Device pointers are plain CUDA device addresses on the context's
+ *     device (for example torch tensors' data_ptr()); they stay owned by the
+ *     caller.  Work is ordered on the context's stream (mapi_config
+ *     .cuda_stream); calls that return host results synchronise that stream
+ *     before returning.
+ *   - Matrices are dense, row-major, with a leading dimension ld >= cols (in
+ *     elements).  Vectors are contiguous; several vectors are column-major
+ *     with a leading dimension.
+ *   - Matrices uploaded with mapi_matrix_upload are copied into a packed,
+ *     library-owned device copy (mapi_mat); free them with mapi_matrix_free or
+ *     mapi_destroy.
+ *   - One context is used by one host thread at a time.
+ *   - Arithmetic on the device is FP32 (float storage) or exact INT32/INT64
+ *     (integer storage); no step uses FP64 on the GPU.
+ *   - On any error the outputs are unspecified and the detail text is
+ *     available from mapi_last_error(ctx).
+ */
+#ifndef MAPI_H
+#define MAPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mapi_ctx mapi_ctx; /* opaque; one per device */
+typedef struct mapi_mat mapi_mat; /* opaque; a packed device matrix */
+
+typedef enum {
+  MAPI_OK = 0,
+  MAPI_EINVAL = 1,     /* bad argument: null pointer, size, op/storage pair */
+  MAPI_ENOMEM = 2,     /* a device or pinned allocation failed */
+  MAPI_EBUDGET = 3,    /* a request can never fit the HBM admission budget */
+  MAPI_EZERONORM = 4,  /* ||A (+) w|| = 0 (e.g. A = 0, or min2 with all signs
+                          opposed); the last good iterate is returned */
+  MAPI_ENONFINITE = 5, /* NaN/Inf in an input or a norm */
+  MAPI_EAGAIN = 6,     /* mapi_poll: the request is still running */
+  MAPI_ETIMEOUT = 7,   /* a bounded device wait gave up */
+  MAPI_ECANCELLED = 8, /* the request was cancelled */
+  MAPI_ECUDA = 9,      /* a CUDA runtime call failed */
+  MAPI_ENOTSUP = 10    /* valid but not supported in this build */
+} mapi_status;
+
+/* The vector product used in A (+) w.
+ *   MIN1    Eq. (3)
+ *   MIN2    Eq. (4)
+ *   DIAMOND Eq. (7), read as sum_i sign(w_i) x_i + w_i sign(x_i) (the
+ *           printed formula mixes the letters; the proof of Proposition 1
+ *           fixes this reading).  Test mode: Proposition 1 pins it.
+ *   DOT     the ordinary product: regular power iteration, Eq. (1), which
+ *           also switches the per-step normalisation to the l2 norm. */
+typedef enum {
+  MAPI_OP_MIN1 = 0,
+  MAPI_OP_MIN2 = 1,
+  MAPI_OP_DIAMOND = 2,
+  MAPI_OP_DOT = 3
+} mapi_op;
+
+/* Storage of a packed matrix (the paper fixes none).  Reduced-precision
+ * copies round to nearest even.  Since (c A) (+) w != c (A (+) w), every
+ * scale is an exact power of two and is undone exactly inside the kernels.
+ *   F32             4 B/element
+ *   BF16            2 B/element
+ *   FP8E4M3_ROWPOW2 1 B/element plus one scale 2^k_i per row, k_i the
+ *                   smallest integer with max_j |a_ij| <= 448 * 2^k_i
+ *   I16 / I8        fixed point with one shared exponent q: A_q =
+ *                   RNE(A 2^q), q the largest in [0, 24] with max|A| 2^q <=
+ *                   32767 (I16) or 127 (I8); the whole iteration then runs in
+ *                   exact integers (MIN1/MIN2 only) */
+typedef enum {
+  MAPI_ST_F32 = 0,
+  MAPI_ST_BF16 = 1,
+  MAPI_ST_FP8E4M3_ROWPOW2 = 2,
+  MAPI_ST_I16 = 3,
+  MAPI_ST_I8 = 4
+} mapi_storage;
+
+/* Element type of an upload source. */
+typedef enum { MAPI_SRC_F32 = 0 } mapi_src_dtype;
+
+/* int_scale_log2 value that asks mapi_matrix_upload to pick q itself. */
+#define MAPI_SCALE_AUTO ((int)0x80000000)
+
+/* flags of mapi_iterate */
+#define MAPI_FLAG_FINAL_L2 1u  /* Alg. 1 optional last step: w_T / ||w_T||_2 */
+#define MAPI_FLAG_RAW_START 2u /* use w0 as given; by default w0 is first
+                                  scaled to ||w0||_2 = 1 (Alg. 1 step 1) */
+
+typedef struct {
+  int device;              /* CUDA device ordinal */
+  size_t hbm_budget_bytes; /* admission budget for served requests (0: none) */
+  void* cuda_stream;       /* cudaStream_t for all work; NULL: a stream the
+                              context creates and owns */
+  int max_slots;           /* served requests resident at once (0: 64) */
+  const char* tune_cache_path; /* autotuner cache file, NULL: in memory only */
+} mapi_config;
+
+/* Create a context on cfg->device.  *out receives the handle.
+ * Errors: MAPI_EINVAL (null pointers, bad device), MAPI_ECUDA. */
+mapi_status mapi_create(const mapi_config* cfg, mapi_ctx** out);
+
+/* Release the context, every matrix it owns and its device buffers.
+ * Synchronises the context's stream first. */
+mapi_status mapi_destroy(mapi_ctx* ctx);
+
+/* Static English text for a status code. */
+const char* mapi_status_str(mapi_status s);
+
+/* Detail text of the last failing call on ctx (owned by ctx; "" if none). */
+const char* mapi_last_error(const mapi_ctx* ctx);
+
+/*
+ * Pack a rows x cols matrix into the chosen storage (library-owned device
+ * copy).  src: rows x cols row-major FP32 values with leading dimension ld
+ * (elements), in device memory if src_is_device else in host memory.
+ * int_scale_log2: q for I16/I8 storage, or MAPI_SCALE_AUTO; ignored for the
+ * float storages.  The packed copy pads every row to a multiple of 16 bytes
+ * (and the row count to a multiple of 64) with zeros; zero entries add
+ * nothing to any product.
+ * Errors: MAPI_EINVAL (sizes, ld < cols, storage, q out of [0, 24] or
+ * entries too large for the integer range), MAPI_ENONFINITE (NaN/Inf
+ * entry), MAPI_ENOMEM, MAPI_ECUDA.
+ */
+mapi_status mapi_matrix_upload(mapi_ctx* ctx, const void* src, int src_is_device,
+                               int src_dtype, int rows, int cols, int64_t ld,
+                               mapi_storage storage, int int_scale_log2,
+                               mapi_mat** out);
+
+/* Free a packed matrix (synchronises the context's stream first). */
+mapi_status mapi_matrix_free(mapi_ctx* ctx, mapi_mat* m);
+
+/* Shape and storage of a packed matrix; any output pointer may be NULL.
+ * int_scale_log2 receives q for integer storage, 0 otherwise; ld_elems the
+ * padded row length in elements. */
+mapi_status mapi_matrix_info(const mapi_mat* m, int* rows, int* cols,
+                             int64_t* ld_elems, int* storage,
+                             int* int_scale_log2);
+
+/* Read back the values the packed copy represents, dequantised exactly, as
+ * doubles: host_out is a caller-owned host array of rows x cols (row-major,
+ * leading dimension cols).  For FP8 storage row_exp (host, rows ints, may be
+ * NULL) receives the exponents k_i.  Synchronous. */
+mapi_status mapi_matrix_download(mapi_ctx* ctx, const mapi_mat* m,
+                                 double* host_out, int* row_exp);
+
+/*
+ * Algorithm 1 (MAPI), or regular power iteration with MAPI_OP_DOT, on a
+ * square packed matrix A (n x n), for nvec independent start vectors that
+ * share every read of A (nvec in 1..8).
+ *   w0     device, n x nvec column-major FP32 with leading dimension ldw
+ *          (>= n): the start vectors, scaled to unit l2 norm first unless
+ *          MAPI_FLAG_RAW_START (Alg. 1 step 1).
+ *   Each step: y = A (+) w (Alg. 1 step 3), w = y / ||y||_1 (step 4; the l2
+ *   norm for MAPI_OP_DOT), delta = ||w_new - w_old||_1.  A vector stops
+ *   after max_iters steps or once delta < tol_l1 (tol_l1 <= 0: never).
+ *   w_out  device, n x nvec column-major (leading dimension ldw): the last
+ *          iterate, l2-normalised if MAPI_FLAG_FINAL_L2 (Alg. 1 step 6).
+ *   iters_done, last_delta: host arrays of nvec entries (may be NULL).
+ * Integer storage: w0 is quantised to RNE(w0 2^q), l1-normalised by the
+ * integer rule w_i = sign(y_i) floor((|y_i| 2^q + floor(L/2)) / L), and
+ * every step runs in exact integers with the same rule (the n divisions of
+ * §2.2); w_out holds w_q 2^-q exactly.  Only MIN1/MIN2 are allowed there.
+ * Errors: MAPI_EINVAL (shape, op/storage pair, nvec), MAPI_EZERONORM (some
+ * vector hit a zero norm; its last good iterate is returned), MAPI_ENONFINITE,
+ * MAPI_ECUDA.  Synchronous.
+ */
+mapi_status mapi_iterate(mapi_ctx* ctx, const mapi_mat* A, mapi_op op,
+                         int nvec, const float* w0, int64_t ldw, int max_iters,
+                         double tol_l1, unsigned flags, float* w_out,
+                         int* iters_done, double* last_delta);
+
+/*
+ * Min-covariance matrix, Eq. (5): C = (1/denom) X (+) X^T for a packed
+ * X (D x N, columns are samples); op MIN1, MIN2 or DOT (then C is the
+ * ordinary covariance of Eq. (2)).  Eq. (5) uses denom = N, Alg. 2 step 4
+ * uses N - 1.  C_out: device, D x D row-major FP32, caller-owned.
+ * Errors: MAPI_EINVAL, MAPI_ECUDA.  Asynchronous on the context stream.
+ */
+mapi_status mapi_mincov(mapi_ctx* ctx, const mapi_mat* X, mapi_op op,
+                        double denom, float* C_out);
+
+#define MAPI_PCA_MINCOV 0 /* Alg. 2: C = X (+) X^T / denom, deflate, MAPI */
+#define MAPI_PCA_PAIR 1   /* matrix-free: t = X^T (+) w, y = X (+) t / denom */
+
+/*
+ * Top-k principal vectors by MAPI (Alg. 2 steps 4-7, k components).
+ *   MINCOV: C = (1/cov_denom) X (+) X^T once; component c runs Alg. 1 on
+ *     C_c = (I - sum_{m<c} P_m) C, P_m = w_m (+) w_m^T built from the earlier
+ *     l2-normalised components, the product P_m C being ordinary (Alg. 2
+ *     step 6 with the sum form that follows Eq. (2)).
+ *   PAIR: component c iterates y = X (+) (X^T (+) w) / cov_denom on X
+ *     directly (t_n = x_n^T (+) w for every sample n, then y_d = sum_n
+ *     X_dn (+) t_n / cov_denom), deflates y <- y - sum_{m<c} P_m y, and
+ *     normalises (l1; l2 for DOT).  The paper has no such step; it is the
+ *     matrix-free counterpart of C w = X (X^T w) / N.
+ *   Both end every component with the l2 normalisation (§2.2).
+ *   w0: device, D x k column-major raw start vectors (each scaled to unit l2
+ *   norm first).  P_out: device, D x k column-major.  iters_done: host, k
+ *   ints (may be NULL).  tol_l1 <= 0 runs exactly iters_per_vec steps.
+ * Errors: MAPI_EINVAL (k outside 1..min(D, 64), op), MAPI_EZERONORM,
+ * MAPI_ENOMEM, MAPI_ECUDA.  Synchronous.
+ */
+mapi_status mapi_pca_topk(mapi_ctx* ctx, const mapi_mat* X, int k, int mode,
+                          mapi_op op, int iters_per_vec, double tol_l1,
+                          double cov_denom, const float* w0, float* P_out,
+                          int* iters_done);
+
+/*
+ * Google matrix of §3.3, Eq. (11), packed in the chosen storage:
+ * G = alpha H + (1 - alpha)/n 1, H column-stochastic with H_ij =
+ * (#links j -> i)/outdeg(j), dangling columns uniform (1/n).  The graph is
+ * out-link CSR in device memory: the targets of node j are
+ * indices[indptr[j] .. indptr[j+1]) (int32, n+1 and nnz entries).
+ * Errors: MAPI_EINVAL (n, alpha outside [0, 1], index out of range is not
+ * checked on the device: the caller guarantees 0 <= indices < n),
+ * MAPI_ENOMEM, MAPI_ECUDA.
+ */
+mapi_status mapi_google_matrix(mapi_ctx* ctx, const int* indptr,
+                               const int* indices, int n, double alpha,
+                               mapi_storage storage, mapi_mat** out);
+
+/*
+ * MAPI-PageRank (§3.3): builds G as mapi_google_matrix does, runs Alg. 1
+ * with op from w0 (device, n FP32) and ends with one l2 normalisation, as
+ * the paper does "for easier comparison".  rank_out: device, n FP32.
+ * iters_done / last_delta: host scalars (may be NULL).  Synchronous.
+ */
+mapi_status mapi_pagerank(mapi_ctx* ctx, const int* indptr, const int* indices,
+                          int n, double alpha, mapi_storage storage,
+                          mapi_op op, const float* w0, int max_iters,
+                          double tol_l1, float* rank_out, int* iters_done,
+                          double* last_delta);
+
+
+/* ------------------------------------------------------------------ */
+/* Diagnostics: kernel timing and launch counting.  Not part of the    */
+/* paper's method; they let a caller measure the kernels against their */
+/* rooflines without an external profiler.                             */
+/* ------------------------------------------------------------------ */
+
+/* Kernel classes timed by mapi_profile. */
+typedef enum {
+  MAPI_KC_GEMV = 0,        /* K1 MAVP-GEMV step (Alg. 1 steps 3-4) */
+  MAPI_KC_PAIR = 1,        /* pair-step partials over X */
+  MAPI_KC_PAIR_FINISH = 2, /* pair-step reduction, deflation, normalisation */
+  MAPI_KC_MINCOV = 3,      /* min-covariance build, Eq. (5) */
+  MAPI_KC_COUNT = 4
+} mapi_kernel_class;
+
+typedef struct {
+  uint64_t launches;             /* kernels launched by the library (each node
+                                    of a replayed CUDA graph counts once) */
+  uint64_t timed[MAPI_KC_COUNT]; /* launches timed, per class */
+  double ms[MAPI_KC_COUNT];      /* summed device durations of those launches */
+  double bytes[MAPI_KC_COUNT];   /* algorithmic bytes they had to read: the
+                                    stored matrix once per launch */
+  double terms[MAPI_KC_COUNT];   /* algorithmic vector-product terms evaluated */
+} mapi_stats;
+
+/* enable != 0: bracket every launch of the classes above with CUDA events
+ * recorded on the stream the kernel is launched on (inside CUDA graphs as
+ * event nodes); durations are collected when the synchronous call that
+ * launched them returns.  Adds a few microseconds per timed launch. */
+mapi_status mapi_profile(mapi_ctx* ctx, int enable);
+
+/* Copy the counters to *out (may be NULL) and, if reset != 0, zero them. */
+mapi_status mapi_get_stats(mapi_ctx* ctx, mapi_stats* out, int reset);
+
+#ifdef __cplusplus
+} /* extern "C" */
+#endif
+
+#endif /* MAPI_H */

@@ -1,0 +1,307 @@
+"""Python binding of libmapi.so (include/mapi.h): MAPI on GB300.
+
+Multiplication-avoiding power iteration (Pan et al., arXiv 2110.12065) runs
+entirely in the CUDA library; this module only marshals arguments through
+ctypes.  Every function has the name of the C entry point it calls.  Device
+arrays are torch CUDA tensors (PyTorch provides device memory and streams);
+host arrays are numpy.  A non-OK status raises ``MapiError``.
+
+There is no CPU fallback: importing this package without the compiled
+library raises ImportError (build it with ``build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+__all__ = [
+    "MapiError", "load", "mapi_create", "mapi_destroy", "mapi_status_str",
+    "mapi_last_error", "mapi_matrix_upload", "mapi_matrix_free",
+    "mapi_matrix_info", "mapi_matrix_download", "mapi_iterate", "mapi_mincov",
+    "mapi_pca_topk", "mapi_google_matrix", "mapi_pagerank", "mapi_profile",
+    "mapi_get_stats", "KERNEL_CLASSES",
+    "OP", "ST", "FLAG_FINAL_L2", "FLAG_RAW_START", "SCALE_AUTO",
+    "PCA_MINCOV", "PCA_PAIR", "STATUS",
+]
+
+OP = {"min1": 0, "min2": 1, "diamond": 2, "dot": 3}
+ST = {"f32": 0, "bf16": 1, "fp8": 2, "i16": 3, "i8": 4}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EBUDGET", 4: "EZERONORM",
+          5: "ENONFINITE", 6: "EAGAIN", 7: "ETIMEOUT", 8: "ECANCELLED",
+          9: "ECUDA", 10: "ENOTSUP"}
+FLAG_FINAL_L2 = 1
+FLAG_RAW_START = 2
+SCALE_AUTO = -(2 ** 31)
+PCA_MINCOV, PCA_PAIR = 0, 1
+_CUDA_STREAM_LEGACY = 1
+
+LIB_PATH = _build_mod.LIB
+_lib = None
+
+
+class MapiError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = "", partial=None):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        self.partial = partial
+        super().__init__(f"{where}: {self.name} ({detail})")
+
+
+KERNEL_CLASSES = ("gemv", "pair", "pair_finish", "mincov")
+
+
+class _Stats(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("timed", C.c_uint64 * 4), ("ms", C.c_double * 4),
+                ("bytes", C.c_double * 4), ("terms", C.c_double * 4)]
+
+
+class _Config(C.Structure):
+    _fields_ = [("device", C.c_int), ("hbm_budget_bytes", C.c_size_t),
+                ("cuda_stream", C.c_void_p), ("max_slots", C.c_int),
+                ("tune_cache_path", C.c_char_p)]
+
+
+def load(path: str | None = None):
+    """Load libmapi.so (raises ImportError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libmapi.so not built ({p}); run paper_2110_12065_gb300.build.build()")
+    lib = C.CDLL(p)
+    i, p_, i64, d, u = C.c_int, C.c_void_p, C.c_int64, C.c_double, C.c_uint
+    sigs = {
+        "mapi_create": [C.POINTER(_Config), C.POINTER(p_)],
+        "mapi_destroy": [p_],
+        "mapi_status_str": [i],
+        "mapi_last_error": [p_],
+        "mapi_matrix_upload": [p_, p_, i, i, i, i, i64, i, i, C.POINTER(p_)],
+        "mapi_matrix_free": [p_, p_],
+        "mapi_matrix_info": [p_, p_, p_, p_, p_, p_],
+        "mapi_matrix_download": [p_, p_, p_, p_],
+        "mapi_iterate": [p_, p_, i, i, p_, i64, i, d, u, p_, p_, p_],
+        "mapi_mincov": [p_, p_, i, d, p_],
+        "mapi_pca_topk": [p_, p_, i, i, i, i, d, d, p_, p_, p_],
+        "mapi_google_matrix": [p_, p_, p_, i, d, i, C.POINTER(p_)],
+        "mapi_pagerank": [p_, p_, p_, i, d, i, i, p_, i, d, p_, p_, p_],
+        "mapi_profile": [p_, i],
+        "mapi_get_stats": [p_, C.POINTER(_Stats), i],
+    }
+    for name, args in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.mapi_status_str.restype = C.c_char_p
+    lib.mapi_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str, ctx=None, partial=None):
+    if st != 0:
+        detail = ""
+        if ctx is not None:
+            detail = (load().mapi_last_error(ctx) or b"").decode(errors="replace")
+        raise MapiError(st, where, detail, partial)
+
+
+def _dptr(t) -> int:
+    """Device address of a torch CUDA tensor (checks contiguity and device)."""
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def mapi_status_str(status: int) -> str:
+    return load().mapi_status_str(int(status)).decode()
+
+
+def mapi_last_error(ctx) -> str:
+    return (load().mapi_last_error(ctx) or b"").decode(errors="replace")
+
+
+def mapi_create(device: int = 0, stream=None, hbm_budget_bytes: int = 0,
+                max_slots: int = 0, tune_cache_path: str | None = None):
+    """Create a context.  ``stream`` is a torch.cuda.Stream (default: torch's
+    current stream, so library work is ordered with the caller's)."""
+    lib = load()
+    if stream is None:
+        stream = _torch().cuda.current_stream(device)
+    handle = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    if handle == 0:
+        handle = _CUDA_STREAM_LEGACY
+    cfg = _Config(int(device), int(hbm_budget_bytes), C.c_void_p(handle), int(max_slots),
+                  tune_cache_path.encode() if tune_cache_path else None)
+    out = C.c_void_p()
+    _check(lib.mapi_create(C.byref(cfg), C.byref(out)), "mapi_create")
+    return out
+
+
+def mapi_destroy(ctx) -> None:
+    _check(load().mapi_destroy(ctx), "mapi_destroy")
+
+
+def mapi_matrix_upload(ctx, src, storage="f32", int_scale_log2: int = SCALE_AUTO):
+    """Pack a 2-D FP32 matrix (torch CUDA tensor or numpy host array)."""
+    lib = load()
+    st = ST[storage] if isinstance(storage, str) else int(storage)
+    out = C.c_void_p()
+    if isinstance(src, np.ndarray):
+        a = np.ascontiguousarray(src, dtype=np.float32)
+        rows, cols = a.shape
+        r = lib.mapi_matrix_upload(ctx, a.ctypes.data_as(C.c_void_p), 0, 0, rows, cols, cols,
+                                   st, int(int_scale_log2), C.byref(out))
+    else:
+        torch = _torch()
+        if src.dtype != torch.float32 or src.dim() != 2:
+            raise ValueError("expected a 2-D float32 tensor")
+        rows, cols = src.shape
+        ld = src.stride(0)
+        if src.stride(1) != 1:
+            raise ValueError("rows must be contiguous")
+        if src.is_cuda:
+            r = lib.mapi_matrix_upload(ctx, C.c_void_p(src.data_ptr()), 1, 0, rows, cols, ld, st,
+                                       int(int_scale_log2), C.byref(out))
+        else:
+            r = lib.mapi_matrix_upload(ctx, C.c_void_p(src.data_ptr()), 0, 0, rows, cols, ld, st,
+                                       int(int_scale_log2), C.byref(out))
+    _check(r, "mapi_matrix_upload", ctx)
+    return out
+
+
+def mapi_matrix_free(ctx, mat) -> None:
+    _check(load().mapi_matrix_free(ctx, mat), "mapi_matrix_free", ctx)
+
+
+def mapi_matrix_info(mat) -> dict:
+    rows, cols, stg, q = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    ld = C.c_int64()
+    _check(load().mapi_matrix_info(mat, C.byref(rows), C.byref(cols), C.byref(ld),
+                                   C.byref(stg), C.byref(q)), "mapi_matrix_info")
+    return {"rows": rows.value, "cols": cols.value, "ld": ld.value,
+            "storage": stg.value, "int_scale_log2": q.value}
+
+
+def mapi_matrix_download(ctx, mat):
+    """(dequantised values as float64 numpy, FP8 row exponents or None)."""
+    info = mapi_matrix_info(mat)
+    out = np.empty((info["rows"], info["cols"]), dtype=np.float64)
+    ex = np.empty(info["rows"], dtype=np.int32) if info["storage"] == ST["fp8"] else None
+    _check(load().mapi_matrix_download(
+        ctx, mat, out.ctypes.data_as(C.c_void_p),
+        ex.ctypes.data_as(C.c_void_p) if ex is not None else None),
+        "mapi_matrix_download", ctx)
+    return out, ex
+
+
+def mapi_iterate(ctx, A, op, w0, max_iters: int, tol_l1: float = 0.0,
+                 flags: int = 0, w_out=None):
+    """Alg. 1 (or RPI with op='dot') on packed A for the start vectors w0
+    (torch CUDA float32, shape (n,) or (nvec, n)).  Returns
+    (w_out like w0, iters_done list, last_delta list)."""
+    torch = _torch()
+    opi = OP[op] if isinstance(op, str) else int(op)
+    squeeze = w0.dim() == 1
+    w = w0.reshape(1, -1) if squeeze else w0
+    if w.dtype != torch.float32:
+        raise ValueError("w0 must be float32")
+    nvec, n = w.shape
+    if w_out is None:
+        w_out = torch.empty_like(w)
+    it = (C.c_int * nvec)()
+    dl = (C.c_double * nvec)()
+    st = load().mapi_iterate(ctx, A, opi, nvec, C.c_void_p(_dptr(w)), n, int(max_iters),
+                             float(tol_l1), int(flags), C.c_void_p(_dptr(w_out)), it, dl)
+    res = (w_out.reshape(-1) if squeeze else w_out, list(it), list(dl))
+    _check(st, "mapi_iterate", ctx, partial=res)
+    return res
+
+
+def mapi_mincov(ctx, X, op, denom: float, C_out=None):
+    """C = (1/denom) X (+) X^T (Eq. (5)) for packed X (D x N)."""
+    torch = _torch()
+    D = mapi_matrix_info(X)["rows"]
+    if C_out is None:
+        C_out = torch.empty((D, D), dtype=torch.float32, device="cuda")
+    opi = OP[op] if isinstance(op, str) else int(op)
+    _check(load().mapi_mincov(ctx, X, opi, float(denom), C.c_void_p(_dptr(C_out))),
+           "mapi_mincov", ctx)
+    return C_out
+
+
+def mapi_pca_topk(ctx, X, k: int, mode, op, iters_per_vec: int, cov_denom: float,
+                  w0, tol_l1: float = 0.0, P_out=None):
+    """Top-k MAPI principal vectors.  w0: torch CUDA float32 (k, D) (row c is
+    start vector c, i.e. D x k column-major).  Returns (P (k, D), iters list)."""
+    torch = _torch()
+    m = {"mincov": PCA_MINCOV, "pair": PCA_PAIR}[mode] if isinstance(mode, str) else int(mode)
+    opi = OP[op] if isinstance(op, str) else int(op)
+    if P_out is None:
+        P_out = torch.empty_like(w0)
+    it = (C.c_int * k)()
+    st = load().mapi_pca_topk(ctx, X, int(k), m, opi, int(iters_per_vec), float(tol_l1),
+                              float(cov_denom), C.c_void_p(_dptr(w0)),
+                              C.c_void_p(_dptr(P_out)), it)
+    res = (P_out, list(it))
+    _check(st, "mapi_pca_topk", ctx, partial=res)
+    return res
+
+
+def mapi_google_matrix(ctx, indptr, indices, n: int, alpha: float = 0.85,
+                       storage="f32"):
+    """Pack G = alpha H + (1 - alpha)/n (Eq. (11)) from out-link CSR (torch
+    CUDA int32 tensors)."""
+    out = C.c_void_p()
+    st = ST[storage] if isinstance(storage, str) else int(storage)
+    _check(load().mapi_google_matrix(ctx, C.c_void_p(_dptr(indptr)), C.c_void_p(_dptr(indices)),
+                                     int(n), float(alpha), st, C.byref(out)),
+           "mapi_google_matrix", ctx)
+    return out
+
+
+def mapi_pagerank(ctx, indptr, indices, n: int, w0, max_iters: int,
+                  alpha: float = 0.85, storage="f32", op="min1",
+                  tol_l1: float = 0.0, rank_out=None):
+    """MAPI-PageRank (§3.3).  Returns (rank (n,), iters_done, last_delta)."""
+    torch = _torch()
+    if rank_out is None:
+        rank_out = torch.empty(n, dtype=torch.float32, device="cuda")
+    st = ST[storage] if isinstance(storage, str) else int(storage)
+    opi = OP[op] if isinstance(op, str) else int(op)
+    it, dl = C.c_int(), C.c_double()
+    r = load().mapi_pagerank(ctx, C.c_void_p(_dptr(indptr)), C.c_void_p(_dptr(indices)), int(n),
+                             float(alpha), st, opi, C.c_void_p(_dptr(w0)), int(max_iters),
+                             float(tol_l1), C.c_void_p(_dptr(rank_out)), C.byref(it),
+                             C.byref(dl))
+    res = (rank_out, it.value, dl.value)
+    _check(r, "mapi_pagerank", ctx, partial=res)
+    return res
+
+
+def mapi_profile(ctx, enable: bool = True) -> None:
+    """Time the library's streaming kernels with CUDA events on their stream."""
+    _check(load().mapi_profile(ctx, 1 if enable else 0), "mapi_profile", ctx)
+
+
+def mapi_get_stats(ctx, reset: bool = False) -> dict:
+    """Launch count and, per kernel class, timed launches, summed ms,
+    algorithmic bytes and terms."""
+    st = _Stats()
+    _check(load().mapi_get_stats(ctx, C.byref(st), 1 if reset else 0), "mapi_get_stats", ctx)
+    out = {"launches": int(st.launches)}
+    for i, name in enumerate(KERNEL_CLASSES):
+        out[name] = {"launches": int(st.timed[i]), "ms": float(st.ms[i]),
+                     "bytes": float(st.bytes[i]), "terms": float(st.terms[i])}
+    return out

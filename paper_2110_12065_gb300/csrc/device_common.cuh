@@ -1,0 +1,261 @@
+// Device-side helpers shared by the MAPI kernels: MAVP term functors,
+// storage decoders, streaming loads and deterministic block reductions.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mapi_internal.cuh"
+
+namespace mapi {
+
+// ------------------------------------------------------------- MAVP terms
+//
+// Every float term is evaluated as  s * clamp(a, lo, hi)  accumulated with one
+// fused multiply-add, where (lo, hi, s) depend only on the vector entry w and
+// are prepared once per w and shared by every row of A that meets it:
+//
+//   min1, Eq. (3): sign(a w) min(|a|, |w|) = sign(w) clamp(a, -|w|, |w|)
+//                  -> lo = -|w|, hi = |w|, s = sign(w) (+1 for w = 0)
+//   min2, Eq. (4): 1(sign a = sign w) min(|a|, |w|)
+//                  = sign(w) clamp(a, min(w, 0), max(w, 0))
+//
+// The clamp returns min(|a|, |w|) with a's sign (or 0), the product by
+// s = +-1 is exact and the sum is rounded once, so each term equals the
+// definition exactly; only the order of the FP32 summation differs from a
+// sequential sum.  Diamond (Eq. (7)) and dot (Eq. (1)) are plain arithmetic.
+
+template <int OP>
+struct Op;
+
+template <>
+struct Op<MAPI_OP_MIN1> {
+  struct P {
+    float lo, hi, s;
+  };
+  static __device__ __forceinline__ P prep(float w) {
+    const float c = fabsf(w);
+    return {-c, c, w < 0.f ? -1.f : 1.f};
+  }
+  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
+    return fmaf(fminf(fmaxf(a, p.lo), p.hi), p.s, acc);
+  }
+};
+
+template <>
+struct Op<MAPI_OP_MIN2> {
+  struct P {
+    float lo, hi, s;
+  };
+  static __device__ __forceinline__ P prep(float w) {
+    return {fminf(w, 0.f), fmaxf(w, 0.f), w < 0.f ? -1.f : 1.f};
+  }
+  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
+    return fmaf(fminf(fmaxf(a, p.lo), p.hi), p.s, acc);
+  }
+};
+
+__device__ __forceinline__ float sgnf(float x) {
+  return (float)((x > 0.f) - (x < 0.f));
+}
+
+template <>
+struct Op<MAPI_OP_DIAMOND> {
+  struct P {
+    float w, sw;
+  };
+  static __device__ __forceinline__ P prep(float w) { return {w, sgnf(w)}; }
+  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
+    // sign(a) w + a sign(w)
+    return fmaf(a, p.sw, fmaf(sgnf(a), p.w, acc));
+  }
+};
+
+template <>
+struct Op<MAPI_OP_DOT> {
+  struct P {
+    float w;
+  };
+  static __device__ __forceinline__ P prep(float w) { return {w}; }
+  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
+    return fmaf(a, p.w, acc);
+  }
+};
+
+// Integer terms (exact): the same clamp identity on INT32.
+template <int OP>
+struct IOp;
+
+template <>
+struct IOp<MAPI_OP_MIN1> {
+  struct P {
+    int lo, hi, s;
+  };
+  static __device__ __forceinline__ P prep(int w) {
+    const int c = abs(w);
+    return {-c, c, w < 0 ? -1 : 1};
+  }
+  static __device__ __forceinline__ int term(int a, const P& p, int acc) {
+    return acc + p.s * min(max(a, p.lo), p.hi);
+  }
+};
+
+template <>
+struct IOp<MAPI_OP_MIN2> {
+  struct P {
+    int lo, hi, s;
+  };
+  static __device__ __forceinline__ P prep(int w) {
+    return {min(w, 0), max(w, 0), w < 0 ? -1 : 1};
+  }
+  static __device__ __forceinline__ int term(int a, const P& p, int acc) {
+    return acc + p.s * min(max(a, p.lo), p.hi);
+  }
+};
+
+// --------------------------------------------------------- storage chunks
+// A packed row is read in 16-byte chunks; Chunk<ST>::E elements per chunk.
+template <int ST>
+struct Chunk;
+
+template <>
+struct Chunk<kF32> {
+  static constexpr int E = 4;
+  uint4 raw;
+  __device__ __forceinline__ float get(int e) const {
+    return __uint_as_float((&raw.x)[e]);
+  }
+};
+
+template <>
+struct Chunk<kBF16> {
+  static constexpr int E = 8;
+  uint4 raw;
+  __device__ __forceinline__ float get(int e) const {
+    const uint32_t wd = (&raw.x)[e >> 1];
+    return __uint_as_float((e & 1) ? (wd & 0xFFFF0000u) : (wd << 16));
+  }
+};
+
+// E4M3 byte -> float without rounding: the 7 magnitude bits placed at the
+// top of an FP32 exponent/mantissa field give 2^(e-127) (1.m) for normals and
+// 2^-126 (0.m) for subnormals; a factor 2^120 then maps both onto the E4M3
+// values 2^(e-7) (1.m) and 2^-6 (0.m).  The row scale 2^k is folded into the
+// same (exact) power-of-two factor by the caller.
+__device__ __forceinline__ float e4m3_bits_unscaled(uint32_t b) {
+  return __uint_as_float(((b & 0x7Fu) << 20) | ((b & 0x80u) << 24));
+}
+
+template <>
+struct Chunk<kFP8> {
+  static constexpr int E = 16;
+  uint4 raw;
+  __device__ __forceinline__ float get(int e) const {
+    const uint32_t wd = (&raw.x)[e >> 2];
+    return e4m3_bits_unscaled((wd >> ((e & 3) * 8)) & 0xFFu);
+  }
+};
+
+template <>
+struct Chunk<kI16> {
+  static constexpr int E = 8;
+  uint4 raw;
+  __device__ __forceinline__ int get(int e) const {
+    const uint32_t wd = (&raw.x)[e >> 1];
+    return (e & 1) ? ((int)wd >> 16) : ((int)(wd << 16) >> 16);
+  }
+};
+
+template <>
+struct Chunk<kI8> {
+  static constexpr int E = 16;
+  uint4 raw;
+  __device__ __forceinline__ int get(int e) const {
+    const uint32_t wd = (&raw.x)[e >> 2];
+    return (int)(wd << (24 - (e & 3) * 8)) >> 24;
+  }
+};
+
+// Streaming 16-byte load: read once per step, so it bypasses L1 and asks L2
+// to fetch whole 256-byte sectors ahead.
+__device__ __forceinline__ uint4 ld_stream(const void* p) {
+  uint4 r;
+  asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p));
+  return r;
+}
+
+// ------------------------------------------------------ compensated sums
+struct Kahan {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ float value() const { return s - c; }
+};
+
+// Deterministic block sum (fixed butterfly order); every thread gets the
+// result.  `sh` needs 33 floats.  All threads of the block must call it.
+template <int NT>
+__device__ __forceinline__ float block_sum(float v, float* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < NT / 32 ? sh[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[32] = v;
+  }
+  __syncthreads();
+  const float r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+template <int NT>
+__device__ __forceinline__ long long block_sum_i64(long long v, long long* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < NT / 32 ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[32] = v;
+  }
+  __syncthreads();
+  const long long r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// Last-CTA election: every CTA calls this once after writing its outputs;
+// exactly one CTA (the last to arrive) gets true, after a fence that makes
+// every other CTA's writes visible to it.  No CTA waits for another.
+__device__ __forceinline__ bool elect_last_cta(unsigned* counter, unsigned total) {
+  __shared__ unsigned s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(counter, 1u);
+    s_last = (t == total - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  const bool last = s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+}  // namespace mapi

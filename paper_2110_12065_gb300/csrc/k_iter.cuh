@@ -1,0 +1,332 @@
+// MAPI iteration kernels (templated; instantiated per storage in k_iter_*.cu).
+//
+//   k_start_*   Alg. 1 step 1: w0 / ||w0||_2 (or as given; integer storage:
+//               RNE(w0 2^q) then the integer l1 rule), zero padding, control
+//               block reset.
+//   k1_gemv_*   Alg. 1 steps 3-4 in one launch: y = A (+) w row by row (the
+//               O(n^2) part, streamed once from HBM), then the last CTA to
+//               finish normalises: w_new = y / ||y||_1 (Eq. (6); ||y||_2 for
+//               DOT), delta = ||w_new - w_old||_1 and the stop test.
+//   k_finish_*  Alg. 1 step 6 (optional): w_T / ||w_T||_2, written out.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace mapi {
+
+struct GemvArgs {
+  const uint8_t* A;     // rows_pad x ld elements, 16-byte rows
+  int64_t row_bytes;    // ld * element size
+  int chunks;           // 16-byte chunks per row
+  int seg;              // chunks per column split (blockIdx.y)
+  int n;                // logical rows (= cols)
+  int rows_pad;
+  const float* w;       // current iterates (nvec vectors, stride wst)
+  float* w_next;        // next iterates
+  int64_t wst;          // vector stride in elements (>= ld)
+  float* ypart;         // [ksplit][nvec][rows_pad] partial products
+  IterCtl* ctl;
+  const float* row_mult;  // FP8: 2^(120 + k_i) per row; else unused
+  int norm_l2;          // 1 for DOT (Eq. (1)), 0 for the MAVPs (Eq. (6))
+};
+
+constexpr int kEpiThreads = 256;
+
+// Last-CTA epilogue for float storage.  NT threads.
+template <int NT, int V>
+__device__ void epilogue_float(const GemvArgs& g, int ks) {
+  __shared__ float sh[33];
+  for (int v = 0; v < V; ++v) {
+    VecState* st = &g.ctl->v[v];
+    if (*(volatile int*)&st->done) continue;  // uniform: written by earlier launches
+    float* y0 = g.ypart + (int64_t)v * g.rows_pad;
+    Kahan acc;
+    for (int i = threadIdx.x; i < g.n; i += NT) {
+      float yi = __ldcg(y0 + i);
+      for (int k = 1; k < ks; ++k) yi += __ldcg(g.ypart + ((int64_t)k * V + v) * g.rows_pad + i);
+      if (ks > 1) y0[i] = yi;
+      acc.add(g.norm_l2 ? yi * yi : fabsf(yi));
+    }
+    float L = block_sum<NT>(acc.value(), sh);
+    if (g.norm_l2) L = sqrtf(L);
+    if (!(L > 0.f) || !isfinite(L)) {
+      if (threadIdx.x == 0) {
+        st->status = (L == 0.f) ? MAPI_EZERONORM : MAPI_ENONFINITE;
+        st->done = 1;
+      }
+      continue;
+    }
+    const float* wo = g.w + (int64_t)v * g.wst;
+    float* wn = g.w_next + (int64_t)v * g.wst;
+    Kahan dl;
+    for (int i = threadIdx.x; i < g.n; i += NT) {
+      const float yi = (ks > 1) ? y0[i] : __ldcg(y0 + i);
+      const float x = yi / L;  // the n divisions of §2.2
+      dl.add(fabsf(x - wo[i]));
+      wn[i] = x;
+    }
+    const float D = block_sum<NT>(dl.value(), sh);
+    if (threadIdx.x == 0) {
+      st->iters += 1;
+      st->delta = D;
+      st->norm = L;
+      if (g.ctl->tol > 0.f && D < g.ctl->tol) st->done = 1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int all = 1;
+    for (int v = 0; v < V; ++v) all &= ((volatile int*)&g.ctl->v[v].done)[0];
+    g.ctl->all_done = all;
+    g.ctl->counter = 0;
+    __threadfence();
+  }
+}
+
+// K1: y = A (+) w for V vectors, R rows per warp, WARPS warps per CTA.
+template <int OP, int ST, int V, int R, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    k1_gemv_float(GemvArgs g) {
+  if (*(volatile int*)&g.ctl->all_done) return;
+  using Ch = Chunk<ST>;
+  constexpr int E = Ch::E;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row0 = (blockIdx.x * WARPS + warp) * R;
+  const int ks = blockIdx.y;
+  const int c_beg = ks * g.seg;
+  const int c_end = min(g.chunks, c_beg + g.seg);
+
+  float acc[R][V][2];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[r][v][0] = acc[r][v][1] = 0.f;
+
+  float mult[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) mult[r] = (ST == kFP8) ? g.row_mult[row0 + r] : 1.f;
+
+  const uint8_t* arow = g.A + (int64_t)row0 * g.row_bytes;
+
+  auto consume = [&](const Ch (&ch)[R], int c) {
+#pragma unroll
+    for (int grp = 0; grp < E / 4; ++grp) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const float4 wv = __ldg(reinterpret_cast<const float4*>(
+            g.w + (int64_t)v * g.wst + (int64_t)c * E + grp * 4));
+        const auto p0 = Op<OP>::prep(wv.x);
+        const auto p1 = Op<OP>::prep(wv.y);
+        const auto p2 = Op<OP>::prep(wv.z);
+        const auto p3 = Op<OP>::prep(wv.w);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          float a0 = ch[r].get(grp * 4 + 0), a1 = ch[r].get(grp * 4 + 1);
+          float a2 = ch[r].get(grp * 4 + 2), a3 = ch[r].get(grp * 4 + 3);
+          if (ST == kFP8) {
+            a0 *= mult[r];
+            a1 *= mult[r];
+            a2 *= mult[r];
+            a3 *= mult[r];
+          }
+          acc[r][v][0] = Op<OP>::term(a0, p0, acc[r][v][0]);
+          acc[r][v][1] = Op<OP>::term(a1, p1, acc[r][v][1]);
+          acc[r][v][0] = Op<OP>::term(a2, p2, acc[r][v][0]);
+          acc[r][v][1] = Op<OP>::term(a3, p3, acc[r][v][1]);
+        }
+      }
+    }
+  };
+
+  int c = c_beg + lane;
+  // two chunks per row in flight per lane
+  for (; c + 32 < c_end; c += 64) {
+    Ch x[R], z[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      x[r].raw = ld_stream(arow + r * g.row_bytes + (int64_t)c * 16);
+      z[r].raw = ld_stream(arow + r * g.row_bytes + (int64_t)(c + 32) * 16);
+    }
+    consume(x, c);
+    consume(z, c + 32);
+  }
+  if (c < c_end) {
+    Ch x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r].raw = ld_stream(arow + r * g.row_bytes + (int64_t)c * 16);
+    consume(x, c);
+  }
+
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      float s = acc[r][v][0] + acc[r][v][1];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) g.ypart[((int64_t)ks * V + v) * g.rows_pad + row0 + r] = s;
+    }
+
+  if (!elect_last_cta(&g.ctl->counter, gridDim.x * gridDim.y)) return;
+  epilogue_float<WARPS * 32, V>(g, gridDim.y);
+}
+
+// ------------------------------------------------------------ integer path
+// w and y are INT32 in units of 2^-q; the w buffers are reinterpreted.
+struct IGemvArgs {
+  GemvArgs g;
+  int q;
+};
+
+template <int NT, int V>
+__device__ void epilogue_int(const IGemvArgs& a, int ks) {
+  const GemvArgs& g = a.g;
+  __shared__ long long sh[33];
+  const int* ypart = reinterpret_cast<const int*>(g.ypart);
+  for (int v = 0; v < V; ++v) {
+    VecState* st = &g.ctl->v[v];
+    if (*(volatile int*)&st->done) continue;
+    int* y0 = reinterpret_cast<int*>(g.ypart) + (int64_t)v * g.rows_pad;
+    long long s = 0;
+    for (int i = threadIdx.x; i < g.n; i += NT) {
+      int yi = __ldcg(y0 + i);
+      for (int k = 1; k < ks; ++k) yi += __ldcg(ypart + ((int64_t)k * V + v) * g.rows_pad + i);
+      if (ks > 1) y0[i] = yi;
+      s += (long long)abs(yi);
+    }
+    const long long L = block_sum_i64<NT>(s, sh);
+    if (L == 0) {
+      if (threadIdx.x == 0) {
+        st->status = MAPI_EZERONORM;
+        st->done = 1;
+      }
+      continue;
+    }
+    const int* wo = reinterpret_cast<const int*>(g.w) + (int64_t)v * g.wst;
+    int* wn = reinterpret_cast<int*>(g.w_next) + (int64_t)v * g.wst;
+    long long d = 0;
+    const long long half = L / 2;
+    for (int i = threadIdx.x; i < g.n; i += NT) {
+      const int yi = (ks > 1) ? y0[i] : __ldcg(y0 + i);
+      const long long m = (((long long)abs(yi) << a.q) + half) / L;
+      const int x = yi < 0 ? -(int)m : (int)m;
+      d += (long long)abs(x - wo[i]);
+      wn[i] = x;
+    }
+    const long long D = block_sum_i64<NT>(d, sh);
+    if (threadIdx.x == 0) {
+      st->iters += 1;
+      st->idelta = D;
+      st->delta = (float)D;
+      if (g.ctl->itol > 0 && D < g.ctl->itol) st->done = 1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int all = 1;
+    for (int v = 0; v < V; ++v) all &= ((volatile int*)&g.ctl->v[v].done)[0];
+    g.ctl->all_done = all;
+    g.ctl->counter = 0;
+    __threadfence();
+  }
+}
+
+template <int OP, int ST, int V, int R, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    k1_gemv_int(IGemvArgs a) {
+  const GemvArgs& g = a.g;
+  if (*(volatile int*)&g.ctl->all_done) return;
+  using Ch = Chunk<ST>;
+  constexpr int E = Ch::E;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row0 = (blockIdx.x * WARPS + warp) * R;
+  const int ks = blockIdx.y;
+  const int c_beg = ks * g.seg;
+  const int c_end = min(g.chunks, c_beg + g.seg);
+  int acc[R][V];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[r][v] = 0;
+  const uint8_t* arow = g.A + (int64_t)row0 * g.row_bytes;
+  const int* w = reinterpret_cast<const int*>(g.w);
+  for (int c = c_beg + lane; c < c_end; c += 32) {
+    Ch x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r].raw = ld_stream(arow + r * g.row_bytes + (int64_t)c * 16);
+#pragma unroll
+    for (int grp = 0; grp < E / 4; ++grp) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int4 wv = __ldg(reinterpret_cast<const int4*>(w + (int64_t)v * g.wst + (int64_t)c * E + grp * 4));
+        const auto p0 = IOp<OP>::prep(wv.x);
+        const auto p1 = IOp<OP>::prep(wv.y);
+        const auto p2 = IOp<OP>::prep(wv.z);
+        const auto p3 = IOp<OP>::prep(wv.w);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          int s = acc[r][v];
+          s = IOp<OP>::term(x[r].get(grp * 4 + 0), p0, s);
+          s = IOp<OP>::term(x[r].get(grp * 4 + 1), p1, s);
+          s = IOp<OP>::term(x[r].get(grp * 4 + 2), p2, s);
+          s = IOp<OP>::term(x[r].get(grp * 4 + 3), p3, s);
+          acc[r][v] = s;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      int s = acc[r][v];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0)
+        reinterpret_cast<int*>(g.ypart)[((int64_t)ks * V + v) * g.rows_pad + row0 + r] = s;
+    }
+  if (!elect_last_cta(&g.ctl->counter, gridDim.x * gridDim.y)) return;
+  epilogue_int<WARPS * 32, V>(a, gridDim.y);
+}
+
+// Launch table entry points (defined per storage file).
+using LaunchFn = cudaError_t (*)(dim3 grid, cudaStream_t s, const GemvArgs& g, int q);
+
+LaunchFn gemv_lookup_f32(int op, int V);
+LaunchFn gemv_lookup_bf16(int op, int V);
+LaunchFn gemv_lookup_fp8(int op, int V);
+LaunchFn gemv_lookup_int(int st, int op, int V);
+
+constexpr int kR = 2;      // rows per warp
+constexpr int kWarps = 8;  // warps per CTA
+
+}  // namespace mapi
+
+// Instantiate the float launch table for one storage tag.
+#define MAPI_DEFINE_FLOAT_TABLE(FNNAME, ST)                                        \
+  namespace mapi {                                                                \
+  template <int OP, int V>                                                        \
+  static cudaError_t launch_##FNNAME(dim3 grid, cudaStream_t s, const GemvArgs& g, \
+                                     int) {                                       \
+    k1_gemv_float<OP, ST, V, kR, kWarps><<<grid, kWarps * 32, 0, s>>>(g);         \
+    return cudaGetLastError();                                                    \
+  }                                                                               \
+  LaunchFn FNNAME(int op, int V) {                                                \
+    switch (op * 16 + V) {                                                        \
+      case MAPI_OP_MIN1 * 16 + 1: return launch_##FNNAME<MAPI_OP_MIN1, 1>;        \
+      case MAPI_OP_MIN1 * 16 + 2: return launch_##FNNAME<MAPI_OP_MIN1, 2>;        \
+      case MAPI_OP_MIN1 * 16 + 4: return launch_##FNNAME<MAPI_OP_MIN1, 4>;        \
+      case MAPI_OP_MIN1 * 16 + 8: return launch_##FNNAME<MAPI_OP_MIN1, 8>;        \
+      case MAPI_OP_MIN2 * 16 + 1: return launch_##FNNAME<MAPI_OP_MIN2, 1>;        \
+      case MAPI_OP_MIN2 * 16 + 2: return launch_##FNNAME<MAPI_OP_MIN2, 2>;        \
+      case MAPI_OP_MIN2 * 16 + 4: return launch_##FNNAME<MAPI_OP_MIN2, 4>;        \
+      case MAPI_OP_MIN2 * 16 + 8: return launch_##FNNAME<MAPI_OP_MIN2, 8>;        \
+      case MAPI_OP_DOT * 16 + 1: return launch_##FNNAME<MAPI_OP_DOT, 1>;          \
+      case MAPI_OP_DOT * 16 + 2: return launch_##FNNAME<MAPI_OP_DOT, 2>;          \
+      case MAPI_OP_DOT * 16 + 4: return launch_##FNNAME<MAPI_OP_DOT, 4>;          \
+      case MAPI_OP_DOT * 16 + 8: return launch_##FNNAME<MAPI_OP_DOT, 8>;          \
+      case MAPI_OP_DIAMOND * 16 + 1: return launch_##FNNAME<MAPI_OP_DIAMOND, 1>;  \
+    }                                                                             \
+    return nullptr;                                                               \
+  }                                                                               \
+  }

@@ -1,0 +1,34 @@
+// K1 MAVP-GEMV instantiations for integer storage (exact INT32 sums).
+#include "k_iter.cuh"
+
+namespace mapi {
+
+template <int OP, int ST, int V>
+static cudaError_t launch_int(dim3 grid, cudaStream_t s, const GemvArgs& g, int q) {
+  IGemvArgs a{g, q};
+  k1_gemv_int<OP, ST, V, kR, kWarps><<<grid, kWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int ST>
+static LaunchFn lookup_st(int op, int V) {
+  switch (op * 16 + V) {
+    case MAPI_OP_MIN1 * 16 + 1: return launch_int<MAPI_OP_MIN1, ST, 1>;
+    case MAPI_OP_MIN1 * 16 + 2: return launch_int<MAPI_OP_MIN1, ST, 2>;
+    case MAPI_OP_MIN1 * 16 + 4: return launch_int<MAPI_OP_MIN1, ST, 4>;
+    case MAPI_OP_MIN1 * 16 + 8: return launch_int<MAPI_OP_MIN1, ST, 8>;
+    case MAPI_OP_MIN2 * 16 + 1: return launch_int<MAPI_OP_MIN2, ST, 1>;
+    case MAPI_OP_MIN2 * 16 + 2: return launch_int<MAPI_OP_MIN2, ST, 2>;
+    case MAPI_OP_MIN2 * 16 + 4: return launch_int<MAPI_OP_MIN2, ST, 4>;
+    case MAPI_OP_MIN2 * 16 + 8: return launch_int<MAPI_OP_MIN2, ST, 8>;
+  }
+  return nullptr;
+}
+
+LaunchFn gemv_lookup_int(int st, int op, int V) {
+  if (st == kI16) return lookup_st<kI16>(op, V);
+  if (st == kI8) return lookup_st<kI8>(op, V);
+  return nullptr;
+}
+
+}  // namespace mapi

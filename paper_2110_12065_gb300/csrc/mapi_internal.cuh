@@ -1,0 +1,205 @@
+// Internal declarations of the MAPI CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/mapi.h"
+
+namespace mapi {
+
+constexpr int kMaxVec = 8;  // start vectors sharing one read of A
+
+// Per-vector state of one solve, resident on the device.
+struct VecState {
+  int done;     // 1 once converged, stopped or failed: later steps skip it
+  int status;   // mapi_status of this vector
+  int iters;    // products (Alg. 1 step 3) completed
+  int pad_;
+  float delta;  // last ||w_new - w_old||_1 (float storage)
+  float norm;   // last ||y|| used for the normalisation
+  long long idelta;  // last delta in units of 2^-q (integer storage)
+};
+
+// Control block of one solve: the last-CTA ticket, the early-exit flag and
+// the per-vector states.  Lives in device memory, one per solve.
+struct IterCtl {
+  unsigned counter;   // CTAs of the current step that have finished
+  int all_done;       // every vector done: later step kernels return at once
+  int nvec;
+  int pad_;
+  float tol;          // float storage: stop when delta < tol
+  float pad2_;
+  long long itol;     // integer storage: stop when delta < itol
+  VecState v[kMaxVec];
+};
+
+// Element type tags used as template arguments.
+enum StTag { kF32 = 0, kBF16 = 1, kFP8 = 2, kI16 = 3, kI8 = 4 };
+
+inline int elem_bytes(mapi_storage st) {
+  switch (st) {
+    case MAPI_ST_F32: return 4;
+    case MAPI_ST_BF16: return 2;
+    case MAPI_ST_FP8E4M3_ROWPOW2: return 1;
+    case MAPI_ST_I16: return 2;
+    case MAPI_ST_I8: return 1;
+  }
+  return 0;
+}
+inline bool is_int_storage(mapi_storage st) {
+  return st == MAPI_ST_I16 || st == MAPI_ST_I8;
+}
+
+}  // namespace mapi
+
+// Packed device matrix.
+struct mapi_mat {
+  int rows = 0, cols = 0;
+  int rows_pad = 0;        // rows rounded up to a multiple of 64 (zero rows)
+  int64_t ld = 0;          // padded row length in elements (16-byte rows)
+  mapi_storage storage = MAPI_ST_F32;
+  int q = 0;               // integer storage: A_q = RNE(A 2^q)
+  void* data = nullptr;    // rows_pad x ld elements
+  float* row_scale = nullptr;  // FP8: 2^(120 + k_i) per row, the decoder's factor
+  int* row_exp = nullptr;      // FP8: k_i per row
+  size_t bytes = 0;
+  mapi_ctx* owner = nullptr;
+  uint64_t id = 0;         // never reused: keys cached graphs (addresses are reused)
+};
+
+// Device scratch owned by a context; grown on demand.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// One timed launch: events around it on its stream.
+struct ProfMark {
+  int cls;
+  cudaEvent_t a, b;
+  double bytes, terms;
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t last_use = 0;
+  uint64_t nodes = 0;              // kernel launches per replay
+  std::vector<ProfMark> marks;     // event nodes inside the graph
+};
+
+struct mapi_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t hbm_budget = 0;
+  int max_slots = 64;
+  std::string tune_cache_path;
+  std::string last_error;
+  std::set<mapi_mat*> mats;
+
+  // scratch for solves
+  DevBuf ypart, wbuf0, wbuf1, ctl, aux;
+  mapi::IterCtl* ctl_host = nullptr;  // pinned mirror of the control block
+
+  // CUDA-graph cache: key -> executable graph
+  std::map<std::vector<int64_t>, GraphEntry> graphs;
+  uint64_t use_clock = 0;
+  uint64_t next_mat_id = 1;
+  cudaStream_t capture_stream = nullptr;
+
+  // diagnostics
+  bool prof_on = false;
+  bool capturing = false;
+  uint64_t capture_count = 0;             // launches recorded into the graph being captured
+  std::vector<ProfMark> pending;          // marks of direct launches
+  std::vector<ProfMark>* mark_sink = nullptr;  // where new marks go
+  std::vector<cudaEvent_t> ev_pool;
+  mapi_stats stats = {};
+};
+
+namespace mapi {
+
+// ---------------------------------------------------------------- errors
+mapi_status fail(mapi_ctx* ctx, mapi_status s, const std::string& msg);
+mapi_status cuda_fail(mapi_ctx* ctx, cudaError_t e, const char* what);
+#define MAPI_CUDA_TRY(ctx, call)                                  \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return ::mapi::cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+// ---------------------------------------------------------- diagnostics
+// Count kernel launches (not while a graph is being captured).
+inline void count_launch(mapi_ctx* ctx, uint64_t n = 1) {
+  if (ctx->capturing) ctx->capture_count += n;
+  else ctx->stats.launches += n;
+}
+// Start a timed launch: returns the start event (nullptr when profiling is off).
+cudaEvent_t prof_begin(mapi_ctx* ctx, cudaStream_t s);
+// End it: records the stop event and files the mark.
+void prof_end(mapi_ctx* ctx, cudaStream_t s, cudaEvent_t a, int cls, double bytes,
+              double terms);
+// Fold completed marks into the counters (stream already synchronised).
+void prof_collect(mapi_ctx* ctx, std::vector<ProfMark>& marks, bool recycle);
+void destroy_graph(mapi_ctx* ctx, GraphEntry& g);
+
+// Grow a scratch buffer (drops cached graphs when an address changes).
+mapi_status ensure(mapi_ctx* ctx, DevBuf& b, size_t bytes);
+
+// --------------------------------------------------------- kernel launchers
+// Iteration launch parameters chosen per shape (see tune.cu).
+struct GemvPlan {
+  int rows_per_warp;   // R
+  int warps;           // warps per CTA
+  int ksplit;          // column splits
+  int grid_rows;       // CTAs along rows
+};
+GemvPlan plan_gemv(const mapi_ctx* ctx, const mapi_mat* A, int nvec);
+
+// Grow the scratch a solve of A with nvec vectors needs (call before capture).
+mapi_status prepare_solve(mapi_ctx* ctx, const mapi_mat* A, int nvec);
+
+// Enqueue a full solve (start, max_iters steps, finish) on `stream`.
+mapi_status enqueue_solve(mapi_ctx* ctx, cudaStream_t stream, const mapi_mat* A,
+                          mapi_op op, int nvec, const float* w0, int64_t ldw,
+                          int max_iters, double tol, unsigned flags,
+                          float* w_out, int64_t ldo, const int* abort = nullptr);
+
+// Pack kernels.
+mapi_status launch_pack(mapi_ctx* ctx, const float* src_dev, int64_t ld_src,
+                        mapi_mat* m);
+mapi_status launch_unpack_f32(mapi_ctx* ctx, const mapi_mat* m, float* dst_dev);
+mapi_status launch_fp8_rowexp(mapi_ctx* ctx, const float* src, int64_t ld_src,
+                              mapi_mat* m, int* flag_dev);
+mapi_status launch_google(mapi_ctx* ctx, const int* indptr, const int* indices,
+                          int n, double alpha, float* dst, int64_t ld);
+mapi_status launch_check_finite(mapi_ctx* ctx, const float* src, int rows,
+                                int cols, int64_t ld, int* flag_dev);
+mapi_status launch_absmax(mapi_ctx* ctx, const float* src, int rows, int cols,
+                          int64_t ld, unsigned* out_bits_dev);
+
+// Start-vector and finishing kernels of a float solve (solve.cu).
+mapi_status launch_start_float(mapi_ctx* ctx, cudaStream_t s, const float* w0, int64_t ldw,
+                               int n, int nvec, float* wb0, float* wb1, int64_t wst, int raw,
+                               IterCtl* ctl, float tol, const int* abort = nullptr);
+mapi_status launch_finish(mapi_ctx* ctx, cudaStream_t s, const float* wb0, const float* wb1,
+                          int64_t wst, int n, int nvec, const IterCtl* ctl, int final_l2,
+                          int is_int, int q, float* out, int64_t ldo);
+
+// PCA kernels (pca.cu).
+mapi_status launch_mincov_raw(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, float denom,
+                              float* C, int64_t ldc, cudaStream_t s);
+mapi_status run_pca(mapi_ctx* ctx, const mapi_mat* X, int k, int mode,
+                    mapi_op op, int iters, double tol, double denom,
+                    const float* w0, float* P_out, int* iters_done);
+
+}  // namespace mapi

@@ -1,0 +1,127 @@
+"""GPU parity of the PCA path through the C ABI: the min-covariance build
+(Eq. (5)), deflation (Alg. 2 step 6, sum form), the matrix-free pair step and
+the top-k drivers, against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import datagen
+import oracle
+import paper_2110_12065_gb300 as M
+from tests.helpers import rel_l1, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+
+
+def spiked(D, N, seed):
+    return datagen.spiked_pca_data(D, N, seed=seed)
+
+
+@pytest.mark.parametrize("op", ["min1", "min2", "dot"])
+@pytest.mark.parametrize("D,N", [(1, 7), (130, 1000), (300, 777)])
+@pytest.mark.parametrize("st", ["f32", "bf16"])
+def test_mincov_parity(mapi_ctx, op, D, N, st):
+    X = spiked(D, N, seed=D + N)
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(X), st)
+    try:
+        Cg = to_host(M.mapi_mincov(mapi_ctx, mat, op, float(N)))
+        torch.cuda.synchronize()
+        Xs = X.astype(np.float64) if st == "f32" else oracle.quant_bf16(X)
+        Co = oracle.mincov(op, Xs, float(N))
+        assert rel_l1(Cg, Co) <= TOL32
+        np.testing.assert_array_equal(Cg, Cg.T)
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
+
+
+@pytest.mark.parametrize("mode", ["mincov", "pair"])
+@pytest.mark.parametrize("op", ["min1", "min2", "dot"])
+def test_pca_topk_parity(mapi_ctx, mode, op):
+    D, N, k, T = 96, 1500, 3, 40
+    X = spiked(D, N, seed=21)
+    W0 = np.stack([datagen.start_vector(D, seed=200 + c) for c in range(k)])
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(X), "f32")
+    try:
+        st, Po, oits = oracle.pca_topk(mode, op, X.astype(np.float64), k, T, float(N), W0.T)
+        try:
+            P, its = M.mapi_pca_topk(mapi_ctx, mat, k, mode, op, T, float(N), to_dev(W0))
+            gst = 0
+        except M.MapiError as e:
+            (P, its), gst = e.partial, e.status
+        # the method itself may stop on a zero norm (min2 after deflation):
+        # both sides must stop at the same component and step
+        assert gst == st and its == list(oits)
+        P = to_host(P)
+        # components finished before a stop are compared
+        first_stop = next((c for c in range(k) if oits[c] < T), k) if st else k
+        for c in range(first_stop):
+            err = rel_l1(P[c], Po[:, c])
+            assert err <= TOL32, (c, err)
+            assert abs(np.linalg.norm(P[c]) - 1) < 1e-5
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
+
+
+@pytest.mark.parametrize("D", [200, 256, 1000])
+def test_pair_mode_ragged_shapes(mapi_ctx, D):
+    N = 2051  # several column tiles plus a ragged tail
+    X = spiked(D, N, seed=D)
+    W0 = np.stack([datagen.start_vector(D, seed=300 + c) for c in range(2)])
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(X), "f32")
+    try:
+        P, _ = M.mapi_pca_topk(mapi_ctx, mat, 2, "pair", "min1", 5, float(N), to_dev(W0))
+        _, Po, _ = oracle.pca_topk("pair", "min1", X.astype(np.float64), 2, 5, float(N), W0.T)
+        for c in range(2):
+            assert rel_l1(to_host(P)[c], Po[:, c]) <= TOL32
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
+
+
+def test_pair_mode_bf16(mapi_ctx):
+    D, N = 256, 4096
+    X = spiked(D, N, seed=31)
+    W0 = np.stack([datagen.start_vector(D, seed=310 + c) for c in range(2)])
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(X), "bf16")
+    try:
+        P, _ = M.mapi_pca_topk(mapi_ctx, mat, 2, "pair", "min1", 10, float(N), to_dev(W0))
+        P = to_host(P)
+        _, Pd, _ = oracle.pca_topk("pair", "min1", oracle.quant_bf16(X), 2, 10, float(N), W0.T)
+        _, Po, _ = oracle.pca_topk("pair", "min1", X.astype(np.float64), 2, 10, float(N), W0.T)
+        for c in range(2):
+            assert rel_l1(P[c], Pd[:, c]) <= TOL32
+            assert rel_l1(P[c], Po[:, c]) <= 2e-2
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
+
+
+def test_pair_step_full_size(mapi_ctx):
+    """D = 1024, N = 65536 (the PCA workload): one pair step of component 1
+    from the GPU's own start against the oracle's full pair step."""
+    D, N = 1024, 65536
+    X = spiked(D, N, seed=0)
+    w0 = datagen.start_vector(D, seed=1)
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(X), "f32")
+    try:
+        P, _ = M.mapi_pca_topk(mapi_ctx, mat, 1, "pair", "min1", 1, float(N),
+                               to_dev(w0[None, :]))
+        y = oracle.pair_step("min1", X, w0 / np.linalg.norm(w0.astype(np.float64)), float(N))
+        assert rel_l1(to_host(P)[0], y / np.linalg.norm(y)) <= TOL32
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
+
+
+def test_pca_bad_arguments(mapi_ctx):
+    X = spiked(16, 64, seed=1)
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(X), "f32")
+    try:
+        w0 = to_dev(np.ones((17, 16), np.float32))
+        with pytest.raises(M.MapiError):
+            M.mapi_pca_topk(mapi_ctx, mat, 17, "pair", "min1", 3, 64.0, w0)
+        with pytest.raises(M.MapiError):
+            M.mapi_pca_topk(mapi_ctx, mat, 1, "pair", "diamond", 3, 64.0, w0[:1])
+        with pytest.raises(M.MapiError):
+            M.mapi_pca_topk(mapi_ctx, mat, 1, "pair", "min1", 3, 0.0, w0[:1])
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
