@@ -211,6 +211,10 @@ def run_gpu(args, rank, world, local_rank, dist):
                 "algorithmic_bytes_per_launch": pair["bytes"] / pair["launches"],
                 "avg_launch_us": round(pair["ms"] / pair["launches"] * 1e3, 3),
                 "kernel_share_of_step": round(pair["ms"] / ms, 4)}
+    kernels = {name: {"launches": st["launches"],
+                      "avg_us": round(st["ms"] / st["launches"] * 1e3, 3) if st["launches"] else None,
+                      "share_of_step": round(st["ms"] / ms, 4)}
+               for name, st in stats.items() if isinstance(st, dict) and st["launches"]}
 
     # ---- end to end: host (pinned) X -> library upload -> solve -> host P
     Xh = torch.from_numpy(X).pin_memory()
@@ -252,6 +256,7 @@ def run_gpu(args, rank, world, local_rank, dist):
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(stats["launches"]),
+        "kernels": kernels,
         "clocks": clocks,
         "variants": variants,
     }

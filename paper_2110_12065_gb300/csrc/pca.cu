@@ -2,6 +2,8 @@
 // the sum form after Eq. (2)), the matrix-free pair step, and the top-k
 // drivers for both modes.
 #include <cooperative_groups.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 
@@ -169,16 +171,21 @@ __global__ void __launch_bounds__(256)
 
 // ======================================================================
 // K4: pair step partials.  A cluster of 4 CTAs owns a stream of column
-// tiles of X; CTA r of the cluster holds rows [r*RC, (r+1)*RC) of the tile
-// (RC = 8 warps x RW rows) in registers, lane = column (1 FP32 or 2 BF16
-// columns per lane).  Per tile:
+// tiles of X; CTA r of the cluster holds rows [r*RC, (r+1)*RC) of each tile
+// (RC = 8 warps x RW rows).  Tiles arrive in shared memory through a
+// S-stage TMA ring (one elected thread issues cp.async.bulk.tensor.2d with
+// an mbarrier transaction count), so HBM reads run on while the warps
+// compute and synchronise.  Lane = column (1 FP32 or 2 BF16 columns per
+// 32-bit word; every row of a stage is 128 bytes, read conflict-free).
+// Per tile:
 //   t_n   = sum_d term(X_dn, w_d)   (column sums: warp -> CTA via shared
 //           memory -> cluster via DSMEM, in a fixed order)
 //   y_d  += sum_n term(X_dn, t_n)   (row sums kept per lane in registers)
 // At the end each row's 32 lane partials are summed and written once per
 // cluster: ypart[cluster][d].
 // ======================================================================
-constexpr int kPairWarps = 8, kPairCluster = 4;
+constexpr int kPairWarps = 8, kPairCluster = 4, kPairStages = 3;
+constexpr long long kWaitLimitNs = 2000000000LL;  // bounded waits: 2 s
 
 template <int ST>
 struct PairCols;
@@ -198,44 +205,86 @@ struct PairCols<kBF16> {
   }
 };
 
-__device__ __forceinline__ uint32_t ld_stream32(const void* p) {
-  uint32_t r;
-  asm("ld.global.nc.L1::no_allocate.L2::256B.u32 %0, [%1];" : "=r"(r) : "l"(p));
-  return r;
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ long long globaltimer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Bounded wait on an mbarrier phase; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const uint32_t a = smem_u32(bar);
+  long long t0 = 0;
+  for (int i = 0;; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (i == 0) t0 = globaltimer_ns();
+    else if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 
 struct PairArgs {
-  const uint8_t* X;
-  int64_t row_bytes;
-  int rows_pad;   // rows present in memory
   int D;          // logical rows
-  int64_t ld;     // elements per row
   int ntiles;     // column tiles
   int nclusters;
   const float* w;  // current iterate (D entries + zero padding)
   float* ypart;    // [nclusters][D_pad]
   int D_pad;       // rows covered by one cluster (4 * 8 * RW)
-  const IterCtl* ctl;
+  IterCtl* ctl;
 };
 
 template <int OP, int ST, int RW>
-__global__ void __launch_bounds__(kPairWarps * 32)
-    k_pair_partial(PairArgs a) {
+__global__ void __launch_bounds__(kPairWarps * 32, 2)
+    k_pair_partial(const __grid_constant__ CUtensorMap xmap, PairArgs a) {
   if (*(volatile const int*)&a.ctl->all_done) return;
   using PC = PairCols<ST>;
   constexpr int CPL = PC::CPL;
   constexpr int TC = 32 * CPL;   // columns per tile
   constexpr int RC = kPairWarps * RW;
+  constexpr unsigned kStageBytes = RC * 128;
   cg::cluster_group cluster = cg::this_cluster();
   const unsigned crank = cluster.block_rank();
   const int cid = blockIdx.x / kPairCluster;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rbase = (int)crank * RC + warp * RW;  // first row of this warp
 
+  extern __shared__ __align__(1024) uint32_t stage[];   // kPairStages x RC x 32 words
+  __shared__ __align__(8) uint64_t full[kPairStages];
   __shared__ float4 wp[RC];                 // (lo, hi, s, 0) per row of this CTA
   __shared__ float tbuf[kPairWarps][TC];    // per-warp column partials
   __shared__ float cpart[2][TC];            // CTA column partials (DSMEM-visible)
+  __shared__ int s_err;
 
+  const int nmine = a.ntiles > cid ? (a.ntiles - cid + a.nclusters - 1) / a.nclusters : 0;
+  if (threadIdx.x == 0) {
+    s_err = 0;
+    for (int s = 0; s < kPairStages; ++s) mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   for (int r = threadIdx.x; r < RC; r += blockDim.x) {
     const int d = (int)crank * RC + r;
     const float wv = d < a.D ? a.w[d] : 0.f;
@@ -244,32 +293,37 @@ __global__ void __launch_bounds__(kPairWarps * 32)
     else wp[r] = make_float4(p.lo, p.hi, p.s, 0.f);
   }
   __syncthreads();
+  auto issue = [&](int j) {
+    const int s = j % kPairStages;
+    const int tile = cid + j * a.nclusters;
+    mbar_expect_tx(&full[s], kStageBytes);
+    tma_load_2d(stage + (size_t)s * RC * 32, &xmap, tile * TC, (int)crank * RC, &full[s]);
+  };
+  if (threadIdx.x == 0)
+    for (int j = 0; j < nmine && j < kPairStages; ++j) issue(j);
 
   float acc[RW];
 #pragma unroll
   for (int j = 0; j < RW; ++j) acc[j] = 0.f;
 
-  const int eb = (ST == kF32) ? 4 : 2;
-  int parity = 0;
-  for (int tile = cid; tile < a.ntiles; tile += a.nclusters, parity ^= 1) {
-    const int64_t col0 = (int64_t)tile * TC + lane * CPL;
+  for (int j = 0; j < nmine; ++j) {
+    const int s = j % kPairStages;
+    const int par = j & 1;
+    const bool ok = mbar_wait(&full[s], (unsigned)((j / kPairStages) & 1));
+    if (!ok) s_err = 1;
     uint32_t raw[RW];
+    const uint32_t* src = stage + (size_t)s * RC * 32 + (size_t)(warp * RW) * 32 + lane;
 #pragma unroll
-    for (int j = 0; j < RW; ++j) {
-      const int d = rbase + j;
-      raw[j] = (d < a.rows_pad && col0 < a.ld)
-                   ? ld_stream32(a.X + (int64_t)d * a.row_bytes + col0 * eb)
-                   : 0u;
-    }
+    for (int jj = 0; jj < RW; ++jj) raw[jj] = src[jj * 32];
     // column partials over this warp's rows
     float tp[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) tp[c] = 0.f;
 #pragma unroll
-    for (int j = 0; j < RW; ++j) {
+    for (int jj = 0; jj < RW; ++jj) {
       float x[CPL];
-      PC::get(raw[j], x);
-      const float4 q = wp[warp * RW + j];
+      PC::get(raw[jj], x);
+      const float4 q = wp[warp * RW + jj];
       typename Op<OP>::P p;
       if constexpr (OP == MAPI_OP_DOT) p = {q.x};
       else p = {q.x, q.y, q.z};
@@ -279,13 +333,18 @@ __global__ void __launch_bounds__(kPairWarps * 32)
 #pragma unroll
     for (int c = 0; c < CPL; ++c) tbuf[warp][lane * CPL + c] = tp[c];
     __syncthreads();
+    // every warp has read stage s: refill it with tile j + S
+    if (threadIdx.x == 0 && j + kPairStages < nmine && !s_err) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(j + kPairStages);
+    }
     if (warp == 0) {
 #pragma unroll
       for (int c = 0; c < CPL; ++c) {
-        float s = 0.f;
+        float sum = 0.f;
 #pragma unroll
-        for (int w = 0; w < kPairWarps; ++w) s += tbuf[w][lane * CPL + c];
-        cpart[parity][lane * CPL + c] = s;
+        for (int w = 0; w < kPairWarps; ++w) sum += tbuf[w][lane * CPL + c];
+        cpart[par][lane * CPL + c] = sum;
       }
     }
     cluster.sync();
@@ -296,26 +355,32 @@ __global__ void __launch_bounds__(kPairWarps * 32)
       float t = 0.f;
 #pragma unroll
       for (int r = 0; r < kPairCluster; ++r) {
-        const float* rem = cluster.map_shared_rank(&cpart[parity][0], r);
+        const float* rem = cluster.map_shared_rank(&cpart[par][0], r);
         t += rem[lane * CPL + c];
       }
       tpar[c] = Op<OP>::prep(t);
     }
 #pragma unroll
-    for (int j = 0; j < RW; ++j) {
+    for (int jj = 0; jj < RW; ++jj) {
       float x[CPL];
-      PC::get(raw[j], x);
+      PC::get(raw[jj], x);
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) acc[j] = Op<OP>::term(x[c], tpar[c], acc[j]);
+      for (int c = 0; c < CPL; ++c) acc[jj] = Op<OP>::term(x[c], tpar[c], acc[jj]);
     }
   }
   // row sums across the 32 lanes, written once per cluster
 #pragma unroll
-  for (int j = 0; j < RW; ++j) {
-    float s = acc[j];
+  for (int jj = 0; jj < RW; ++jj) {
+    float sum = acc[jj];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) a.ypart[(int64_t)cid * a.D_pad + rbase + j] = s;
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) a.ypart[(int64_t)cid * a.D_pad + rbase + jj] = sum;
+  }
+  if (threadIdx.x == 0 && s_err) {
+    // a tile never arrived: report it; later kernels of the solve stop
+    a.ctl->v[0].status = MAPI_ETIMEOUT;
+    a.ctl->v[0].done = 1;
+    a.ctl->all_done = 1;
   }
   cluster.sync();  // no CTA leaves while a peer may still read its cpart
 }
@@ -494,6 +559,8 @@ struct PairLaunch {
   const void* fn = nullptr;
   int rw = 0;
   int clusters = 0;
+  size_t smem = 0;
+  CUtensorMap map;
 };
 
 template <int OP, int ST>
@@ -506,6 +573,21 @@ static const void* pair_fn(int rw) {
   return nullptr;
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
 static mapi_status plan_pair(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, PairLaunch* pl) {
   const int D = X->rows;
   int rw = 8;
@@ -513,17 +595,40 @@ static mapi_status plan_pair(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, PairL
   if (kPairCluster * kPairWarps * rw < D)
     return fail(ctx, MAPI_EINVAL, "pair mode supports D <= 1024");
   const void* fn = nullptr;
+  CUtensorMapDataType dt;
+  int tc;
   if (X->storage == MAPI_ST_F32) {
     fn = op == MAPI_OP_MIN1 ? pair_fn<MAPI_OP_MIN1, kF32>(rw)
          : op == MAPI_OP_MIN2 ? pair_fn<MAPI_OP_MIN2, kF32>(rw)
                               : pair_fn<MAPI_OP_DOT, kF32>(rw);
+    dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    tc = 32;
   } else if (X->storage == MAPI_ST_BF16) {
     fn = op == MAPI_OP_MIN1 ? pair_fn<MAPI_OP_MIN1, kBF16>(rw)
          : op == MAPI_OP_MIN2 ? pair_fn<MAPI_OP_MIN2, kBF16>(rw)
                               : pair_fn<MAPI_OP_DOT, kBF16>(rw);
+    dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    tc = 64;
   } else {
     return fail(ctx, MAPI_EINVAL, "pair mode supports F32 and BF16 storage");
   }
+  const int rc = kPairWarps * rw;
+  pl->smem = (size_t)kPairStages * rc * 128;
+  MAPI_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)pl->smem));
+  // the tensor map: X as [rows_pad][ld] with a (tc x rc) box; rows and
+  // columns beyond the matrix read as zero
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return fail(ctx, MAPI_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  const int eb = elem_bytes(X->storage);
+  cuuint64_t gdim[2] = {(cuuint64_t)X->ld, (cuuint64_t)X->rows_pad};
+  cuuint64_t gstride[1] = {(cuuint64_t)X->ld * eb};
+  cuuint32_t box[2] = {(cuuint32_t)tc, (cuuint32_t)rc};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(&pl->map, dt, 2, X->data, gdim, gstride, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, MAPI_ECUDA, "tensor map encoding failed");
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -532,7 +637,7 @@ static mapi_status plan_pair(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, PairL
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(kPairCluster * ctx->sm_count, 1, 1);
   cfg.blockDim = dim3(kPairWarps * 32, 1, 1);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = pl->smem;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int nclusters = 0;
@@ -576,11 +681,7 @@ static mapi_status launch_pair_step(mapi_ctx* ctx, cudaStream_t s, const PairLau
                                     float* ypart, const float* Q, int64_t ldq, int fcs,
                                     IterCtl* ctl, int norm_l2, float denom) {
   PairArgs pa;
-  pa.X = (const uint8_t*)X->data;
-  pa.row_bytes = X->ld * elem_bytes(X->storage);
-  pa.rows_pad = X->rows_pad;
   pa.D = X->rows;
-  pa.ld = X->ld;
   const int TC = (X->storage == MAPI_ST_F32) ? 32 : 64;
   pa.ntiles = (int)((X->ld + TC - 1) / TC);
   pa.nclusters = pl.clusters;
@@ -597,10 +698,11 @@ static mapi_status launch_pair_step(mapi_ctx* ctx, cudaStream_t s, const PairLau
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(kPairCluster * pl.clusters, 1, 1);
     cfg.blockDim = dim3(kPairWarps * 32, 1, 1);
+    cfg.dynamicSmemBytes = pl.smem;
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    void* args[] = {&pa};
+    void* args[] = {(void*)&pl.map, &pa};
     cudaEvent_t ev = prof_begin(ctx, s);
     MAPI_CUDA_TRY(ctx, cudaLaunchKernelExC(&cfg, pl.fn, args));
     prof_end(ctx, s, ev, MAPI_KC_PAIR, (double)X->rows * X->cols * elem_bytes(X->storage),

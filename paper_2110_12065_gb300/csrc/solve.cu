@@ -168,7 +168,9 @@ GemvPlan plan_gemv(const mapi_ctx* ctx, const mapi_mat* A, int nvec) {
   p.warps = kWarps;
   p.grid_rows = A->rows_pad / (kR * kWarps);
   const int64_t chunks = A->ld * elem_bytes(A->storage) / 16;
-  const int want = 2 * ctx->sm_count;
+  // enough CTAs for several waves (the block scheduler then balances the
+  // tail), each column split still >= 64 chunks (2 per lane)
+  const int want = 24 * ctx->sm_count;
   int ks = 1;
   while ((int64_t)p.grid_rows * ks < want && chunks / (ks * 2) >= 64) ks *= 2;
   p.ksplit = ks;
