@@ -38,7 +38,7 @@ struct Op<MAPI_OP_MIN1> {
   };
   static __device__ __forceinline__ P prep(float w) {
     const float c = fabsf(w);
-    return {-c, c, w < 0.f ? -1.f : 1.f};
+    return {-c, c, copysignf(1.f, w)};
   }
   static __device__ __forceinline__ float term(float a, const P& p, float acc) {
     return fmaf(fminf(fmaxf(a, p.lo), p.hi), p.s, acc);

@@ -107,7 +107,7 @@ struct mapi_ctx {
   std::set<mapi_mat*> mats;
 
   // scratch for solves
-  DevBuf ypart, wbuf0, wbuf1, ctl, aux;
+  DevBuf ypart, wbuf0, wbuf1, ctl, aux, mcpart;
   mapi::IterCtl* ctl_host = nullptr;  // pinned mirror of the control block
 
   // CUDA-graph cache: key -> executable graph

@@ -15,57 +15,83 @@ namespace mapi {
 
 // ======================================================================
 // K2: C = (1/denom) X (+) X^T.  128 x 128 output tiles (upper triangle of
-// tiles only, mirrored), 256 threads, 8 x 8 register micro-tiles, N swept in
-// chunks of 16 staged through shared memory (k-major, padded rows).
+// tiles only), split over the samples (blockIdx.y) so that every SM has
+// work; 256 threads, 8 x 8 register micro-tiles; the sample range is swept in
+// chunks of 16 through two shared-memory buffers (k-major, padded rows), the
+// next chunk prefetched into registers while the current one is consumed.
+// Each split writes its partial tile; k_mincov_reduce sums the splits in a
+// fixed order, divides by denom and mirrors the tile.
 // ======================================================================
 constexpr int kMcT = 128, kMcK = 16, kMcPad = 4;
 
 template <int ST>
-__device__ __forceinline__ void mc_load_tile(const uint8_t* X, int64_t row_bytes,
-                                             int rows_pad, int64_t ld, int r0, int k0,
-                                             float (*S)[kMcT + kMcPad]) {
-  const int t = threadIdx.x;
-  if (ST == kF32) {
-    // 128 rows x 16 floats = 512 float4; 2 per thread
+struct McStage;
+template <>
+struct McStage<kF32> {  // 128 rows x 16 floats = 512 float4, 2 per thread
+  float4 v[2];
+  __device__ __forceinline__ void load(const uint8_t* X, int64_t row_bytes, int rows_pad,
+                                       int64_t k_end, int r0, int64_t k0) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int idx = t + h * 256;
+      const int idx = threadIdx.x + h * 256;
       const int r = idx >> 2, cc = (idx & 3) * 4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r0 + r < rows_pad && k0 + cc < ld)
-        v = *reinterpret_cast<const float4*>(X + (int64_t)(r0 + r) * row_bytes + (int64_t)(k0 + cc) * 4);
-      S[cc + 0][r] = v.x;
-      S[cc + 1][r] = v.y;
-      S[cc + 2][r] = v.z;
-      S[cc + 3][r] = v.w;
+      v[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r0 + r < rows_pad && k0 + cc < k_end)
+        v[h] = __ldg(reinterpret_cast<const float4*>(X + (int64_t)(r0 + r) * row_bytes +
+                                                     (k0 + cc) * 4));
     }
-  } else {
-    // BF16: 128 rows x 16 = 256 chunks of 8; 1 per thread
-    const int r = t >> 1, cc = (t & 1) * 8;
-    Chunk<kBF16> ch;
-    ch.raw = make_uint4(0, 0, 0, 0);
-    if (r0 + r < rows_pad && k0 + cc < ld)
-      ch.raw = *reinterpret_cast<const uint4*>(X + (int64_t)(r0 + r) * row_bytes + (int64_t)(k0 + cc) * 2);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) S[cc + e][r] = ch.get(e);
   }
-}
+  __device__ __forceinline__ void store(float (*S)[kMcT + kMcPad]) const {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int idx = threadIdx.x + h * 256;
+      const int r = idx >> 2, cc = (idx & 3) * 4;
+      S[cc + 0][r] = v[h].x;
+      S[cc + 1][r] = v[h].y;
+      S[cc + 2][r] = v[h].z;
+      S[cc + 3][r] = v[h].w;
+    }
+  }
+};
+template <>
+struct McStage<kBF16> {  // 128 rows x 16 bf16 = 256 chunks of 8, 1 per thread
+  Chunk<kBF16> c;
+  __device__ __forceinline__ void load(const uint8_t* X, int64_t row_bytes, int rows_pad,
+                                       int64_t k_end, int r0, int64_t k0) {
+    const int r = threadIdx.x >> 1, cc = (threadIdx.x & 1) * 8;
+    c.raw = make_uint4(0, 0, 0, 0);
+    if (r0 + r < rows_pad && k0 + cc < k_end)
+      c.raw = __ldg(reinterpret_cast<const uint4*>(X + (int64_t)(r0 + r) * row_bytes +
+                                                   (k0 + cc) * 2));
+  }
+  __device__ __forceinline__ void store(float (*S)[kMcT + kMcPad]) const {
+    const int r = threadIdx.x >> 1, cc = (threadIdx.x & 1) * 8;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) S[cc + e][r] = c.get(e);
+  }
+};
 
-template <int OP, int ST>
-__global__ void __launch_bounds__(256)
-    k_mincov(const uint8_t* __restrict__ X, int64_t row_bytes, int rows_pad, int64_t ld,
-             int D, float denom, float* __restrict__ C, int64_t ldc) {
-  __shared__ __align__(16) float As[kMcK][kMcT + kMcPad];
-  __shared__ __align__(16) float Bs[kMcK][kMcT + kMcPad];
-  // triangular tile index -> (tp, tq), tp <= tq
-  int b = blockIdx.x, tp = 0;
-  const int T = (D + kMcT - 1) / kMcT;
+__device__ __forceinline__ void mc_tile_of(int b, int T, int& tp, int& tq) {
+  tp = 0;
   while (b >= T - tp) {
     b -= T - tp;
     ++tp;
   }
-  const int tq = tp + b;
+  tq = tp + b;
+}
+
+template <int OP, int ST>
+__global__ void __launch_bounds__(256, 2)
+    k_mincov(const uint8_t* __restrict__ X, int64_t row_bytes, int rows_pad, int64_t ld,
+             int D, int64_t kseg, float* __restrict__ part) {
+  __shared__ __align__(16) float As[2][kMcK][kMcT + kMcPad];
+  __shared__ __align__(16) float Bs[2][kMcK][kMcT + kMcPad];
+  const int T = (D + kMcT - 1) / kMcT;
+  int tp, tq;
+  mc_tile_of(blockIdx.x, T, tp, tq);
   const int p0 = tp * kMcT, q0 = tq * kMcT;
+  const int64_t k_beg = (int64_t)blockIdx.y * kseg;
+  const int64_t k_end = min(ld, k_beg + kseg);
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   float acc[8][8];
 #pragma unroll
@@ -73,16 +99,27 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
-  for (int64_t k0 = 0; k0 < ld; k0 += kMcK) {
-    mc_load_tile<ST>(X, row_bytes, rows_pad, ld, p0, (int)k0, As);
-    mc_load_tile<ST>(X, row_bytes, rows_pad, ld, q0, (int)k0, Bs);
-    __syncthreads();
+  McStage<ST> na, nb;
+  int buf = 0;
+  if (k_beg < k_end) {
+    na.load(X, row_bytes, rows_pad, k_end, p0, k_beg);
+    nb.load(X, row_bytes, rows_pad, k_end, q0, k_beg);
+    na.store(As[0]);
+    nb.store(Bs[0]);
+  }
+  __syncthreads();
+  for (int64_t k0 = k_beg; k0 < k_end; k0 += kMcK) {
+    const bool more = k0 + kMcK < k_end;
+    if (more) {  // prefetch the next chunk into registers
+      na.load(X, row_bytes, rows_pad, k_end, p0, k0 + kMcK);
+      nb.load(X, row_bytes, rows_pad, k_end, q0, k0 + kMcK);
+    }
 #pragma unroll 4
     for (int k = 0; k < kMcK; ++k) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[k][ty * 8]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[k][ty * 8 + 4]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k][tx * 8]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k][tx * 8 + 4]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 8]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 8 + 4]);
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -92,20 +129,38 @@ __global__ void __launch_bounds__(256)
         for (int i = 0; i < 8; ++i) acc[i][j] = Op<OP>::term(a[i], p, acc[i][j]);
       }
     }
+    if (more) {
+      na.store(As[buf ^ 1]);
+      nb.store(Bs[buf ^ 1]);
+    }
     __syncthreads();
+    buf ^= 1;
   }
+  // partial tile: part[split][tile][128][128]
+  float* out = part + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kMcT * kMcT;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const int p = p0 + ty * 8 + i;
-    if (p >= D) continue;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int q = q0 + tx * 8 + j;
-      if (q >= D) continue;
-      const float v = acc[i][j] / denom;
-      C[(int64_t)p * ldc + q] = v;
-      if (tp != tq) C[(int64_t)q * ldc + p] = v;
-    }
+    float4* o = reinterpret_cast<float4*>(out + (ty * 8 + i) * kMcT + tx * 8);
+    o[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    o[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+  }
+}
+
+// Sum the splits of each tile in order, divide by denom, write C and its mirror.
+__global__ void k_mincov_reduce(const float* __restrict__ part, int ntiles, int nsplit, int D,
+                                float denom, float* __restrict__ C, int64_t ldc) {
+  const int T = (D + kMcT - 1) / kMcT;
+  int tp, tq;
+  mc_tile_of(blockIdx.x, T, tp, tq);
+  for (int e = threadIdx.x; e < kMcT * kMcT; e += blockDim.x) {
+    const int i = e / kMcT, j = e % kMcT;
+    const int p = tp * kMcT + i, q = tq * kMcT + j;
+    if (p >= D || q >= D) continue;
+    float s = 0.f;
+    for (int k = 0; k < nsplit; ++k) s += part[((int64_t)k * ntiles + blockIdx.x) * kMcT * kMcT + e];
+    const float v = s / denom;
+    C[(int64_t)p * ldc + q] = v;
+    if (tp != tq) C[(int64_t)q * ldc + p] = v;
   }
 }
 
@@ -521,9 +576,17 @@ mapi_status launch_mincov_raw(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, floa
   const int nt = T * (T + 1) / 2;
   const int64_t rb = X->ld * elem_bytes(X->storage);
   const uint8_t* x = (const uint8_t*)X->data;
+  // split the samples until there are about 4 CTAs per SM (2 resident)
+  int nsplit = 1;
+  while (nt * nsplit < 4 * ctx->sm_count && X->ld / (nsplit * 2) >= 4 * kMcK) nsplit *= 2;
+  const int64_t kseg = ((X->ld + nsplit - 1) / nsplit + kMcK - 1) / kMcK * kMcK;
+  mapi_status st = ensure(ctx, ctx->mcpart, sizeof(float) * (size_t)nsplit * nt * kMcT * kMcT);
+  if (st != MAPI_OK) return st;
+  float* part = (float*)ctx->mcpart.p;
+  const dim3 grid(nt, nsplit);
   cudaEvent_t ev = prof_begin(ctx, s);
 #define MC(OPV, STV) \
-  k_mincov<OPV, STV><<<nt, 256, 0, s>>>(x, rb, X->rows_pad, X->ld, X->rows, denom, C, ldc)
+  k_mincov<OPV, STV><<<grid, 256, 0, s>>>(x, rb, X->rows_pad, X->ld, X->rows, kseg, part)
   if (X->storage == MAPI_ST_F32) {
     if (op == MAPI_OP_MIN1) MC(MAPI_OP_MIN1, kF32);
     else if (op == MAPI_OP_MIN2) MC(MAPI_OP_MIN2, kF32);
@@ -539,6 +602,9 @@ mapi_status launch_mincov_raw(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, floa
   MAPI_CUDA_TRY(ctx, cudaGetLastError());
   prof_end(ctx, s, ev, MAPI_KC_MINCOV, (double)X->rows * X->cols * elem_bytes(X->storage),
            (double)X->rows * (X->rows + 1) / 2 * X->cols);
+  count_launch(ctx);
+  k_mincov_reduce<<<nt, 256, 0, s>>>(part, nt, nsplit, X->rows, denom, C, ldc);
+  MAPI_CUDA_TRY(ctx, cudaGetLastError());
   count_launch(ctx);
   return MAPI_OK;
 }
