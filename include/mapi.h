@@ -284,6 +284,40 @@ mapi_status mapi_profile(mapi_ctx* ctx, int enable);
 /* Copy the counters to *out (may be NULL) and, if reset != 0, zero them. */
 mapi_status mapi_get_stats(mapi_ctx* ctx, mapi_stats* out, int reset);
 
+
+/*
+ * Allocation-free solve.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory, and it calls no
+ * cudaMalloc, cudaFree or any allocating library routine.  Typical callers:
+ * a process whose device memory is already owned by another allocator (a
+ * framework's caching allocator or a pool reserved at start-up, where a raw
+ * cudaMalloc would fail or fragment it), and latency-critical loops that
+ * cannot afford the implicit device synchronisation of cudaMalloc/cudaFree.
+ *
+ * Runs Algorithm 1 like mapi_iterate (one start vector; op MIN1, MIN2,
+ * DIAMOND or DOT; same flags, stop rule and statuses) on the calling thread's
+ * current device, on `cuda_stream` (NULL: the legacy default stream), and
+ * returns after the stream has finished the solve.
+ *   A      device, n x n row-major FP32 with leading dimension lda (elements);
+ *          lda % 4 == 0 and A 16-byte aligned.  Entries between column n and
+ *          lda are never used.  Caller-owned, read only.
+ *   w0     device, n FP32 (caller-owned).
+ *   w_out  device, n FP32 (caller-owned): the last iterate.
+ *   iters_done, last_delta: host scalars (may be NULL).
+ * Limit: n <= 8192; a larger n (or a bad pointer, lda or op) returns
+ * MAPI_EINVAL before anything runs.
+ * Scratch: one static device array of about 320 KiB inside the library,
+ * present on every GPU that loads it until the process exits.  The first
+ * call on a device looks its address up (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Every call reuses the same array
+ * and rewrites what it needs, so calls that overlap on the GPU (other
+ * threads, other streams) race with each other: serialise them.
+ */
+mapi_status mapi_iterate_noalloc(const float* A, int n, int64_t lda, mapi_op op,
+                                 const float* w0, int max_iters, double tol_l1,
+                                 unsigned flags, float* w_out, int* iters_done,
+                                 double* last_delta, void* cuda_stream);
+
 #ifdef __cplusplus
 } /* extern "C" */
 #endif

@@ -23,7 +23,7 @@ __all__ = [
     "mapi_last_error", "mapi_matrix_upload", "mapi_matrix_free",
     "mapi_matrix_info", "mapi_matrix_download", "mapi_iterate", "mapi_mincov",
     "mapi_pca_topk", "mapi_google_matrix", "mapi_pagerank", "mapi_profile",
-    "mapi_get_stats", "KERNEL_CLASSES",
+    "mapi_get_stats", "mapi_iterate_noalloc", "KERNEL_CLASSES",
     "OP", "ST", "FLAG_FINAL_L2", "FLAG_RAW_START", "SCALE_AUTO",
     "PCA_MINCOV", "PCA_PAIR", "STATUS",
 ]
@@ -91,6 +91,7 @@ def load(path: str | None = None):
         "mapi_pagerank": [p_, p_, p_, i, d, i, i, p_, i, d, p_, p_, p_],
         "mapi_profile": [p_, i],
         "mapi_get_stats": [p_, C.POINTER(_Stats), i],
+        "mapi_iterate_noalloc": [p_, i, i64, i, p_, i, d, u, p_, p_, p_, p_],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -305,3 +306,29 @@ def mapi_get_stats(ctx, reset: bool = False) -> dict:
         out[name] = {"launches": int(st.timed[i]), "ms": float(st.ms[i]),
                      "bytes": float(st.bytes[i]), "terms": float(st.terms[i])}
     return out
+
+
+def mapi_iterate_noalloc(A, op, w0, max_iters: int, tol_l1: float = 0.0, flags: int = 0,
+                         w_out=None, stream=None):
+    """Alg. 1 on a caller-owned FP32 device matrix without any allocation in
+    the library (scratch is a fixed static device array; n <= 8192).  A: torch
+    CUDA float32 (n, >= n) with rows 16-byte aligned; w0: (n,).  w_out must be
+    preallocated by callers that cannot allocate.  Returns (w_out, iters, delta)."""
+    torch = _torch()
+    n = A.shape[0]
+    if A.dim() != 2 or A.stride(1) != 1 or A.dtype != torch.float32:
+        raise ValueError("A must be a 2-D float32 tensor with contiguous rows")
+    if w_out is None:
+        w_out = torch.empty(n, dtype=torch.float32, device=A.device)
+    opi = OP[op] if isinstance(op, str) else int(op)
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device)
+    handle = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    it, dl = C.c_int(), C.c_double()
+    st = load().mapi_iterate_noalloc(C.c_void_p(A.data_ptr()), n, A.stride(0), opi,
+                                     C.c_void_p(_dptr(w0)), int(max_iters), float(tol_l1),
+                                     int(flags), C.c_void_p(_dptr(w_out)), C.byref(it),
+                                     C.byref(dl), C.c_void_p(handle or None))
+    res = (w_out, it.value, dl.value)
+    _check(st, "mapi_iterate_noalloc", None, partial=res)
+    return res
