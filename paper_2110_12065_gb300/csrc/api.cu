@@ -105,6 +105,56 @@ void destroy_graph(mapi_ctx* ctx, GraphEntry& g) {
   g.marks.clear();
 }
 
+mapi_status launch_cached_graph(mapi_ctx* ctx, const std::vector<int64_t>& key,
+                                const std::function<mapi_status(cudaStream_t)>& enqueue,
+                                GraphEntry** out) {
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    if (ctx->graphs.size() >= 32) {  // evict the least recently used graph
+      auto victim = ctx->graphs.begin();
+      for (auto j = ctx->graphs.begin(); j != ctx->graphs.end(); ++j)
+        if (j->second.last_use < victim->second.last_use) victim = j;
+      cudaStreamSynchronize(ctx->stream);
+      destroy_graph(ctx, victim->second);
+      ctx->graphs.erase(victim);
+    }
+    GraphEntry entry;
+    cudaGraph_t graph = nullptr;
+    MAPI_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    ctx->capture_count = 0;
+    ctx->mark_sink = &entry.marks;
+    mapi_status s = enqueue(ctx->capture_stream);
+    ctx->capturing = false;
+    ctx->mark_sink = nullptr;
+    entry.nodes = ctx->capture_count;
+    cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+    if (s != MAPI_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      destroy_graph(ctx, entry);
+      cudaGetLastError();
+      return s != MAPI_OK ? s : cuda_fail(ctx, e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&entry.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      destroy_graph(ctx, entry);
+      return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    it = ctx->graphs.emplace(key, std::move(entry)).first;
+  }
+  it->second.last_use = ++ctx->use_clock;
+  MAPI_CUDA_TRY(ctx, cudaGraphLaunch(it->second.exec, ctx->stream));
+  *out = &it->second;
+  return MAPI_OK;
+}
+
+void finish_graph(mapi_ctx* ctx, GraphEntry* g) {
+  ctx->stats.launches += g->nodes;
+  prof_collect(ctx, g->marks, false);
+  prof_collect(ctx, ctx->pending, true);
+}
+
 }  // namespace mapi
 
 namespace {
@@ -289,7 +339,8 @@ mapi_status mapi_create(const mapi_config* cfg, mapi_ctx** out) {
     ctx->own_stream = true;
   }
   if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMallocHost(&ctx->ctl_host, sizeof(IterCtl)) != cudaSuccess) {
+      cudaMallocHost(&ctx->ctl_host, sizeof(IterCtl)) != cudaSuccess ||
+      cudaMallocHost(&ctx->rec_host, sizeof(int) * 256) != cudaSuccess) {
     cudaGetLastError();
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -311,10 +362,12 @@ mapi_status mapi_destroy(mapi_ctx* ctx) {
   prof_collect(ctx, ctx->pending, true);
   std::set<mapi_mat*> ms = ctx->mats;
   for (auto* m : ms) free_matrix(ctx, m);
-  for (DevBuf* b : {&ctx->ypart, &ctx->wbuf0, &ctx->wbuf1, &ctx->ctl, &ctx->aux, &ctx->mcpart})
+  for (DevBuf* b : {&ctx->ypart, &ctx->wbuf0, &ctx->wbuf1, &ctx->ctl, &ctx->aux, &ctx->mcpart,
+                    &ctx->pca_c0, &ctx->pca_c1, &ctx->pca_q, &ctx->pca_defl})
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
+  if (ctx->rec_host) cudaFreeHost(ctx->rec_host);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -438,54 +491,18 @@ mapi_status mapi_iterate(mapi_ctx* ctx, const mapi_mat* A, mapi_op op, int nvec,
                               (int64_t)(uintptr_t)ctx->wbuf0.p,
                               (int64_t)(uintptr_t)ctx->ypart.p,
                               (int64_t)ctx->prof_on};
-  auto it = ctx->graphs.find(key);
-  cudaGraphExec_t exec = nullptr;
-  if (it != ctx->graphs.end()) {
-    exec = it->second.exec;
-    it->second.last_use = ++ctx->use_clock;
-  } else {
-    if (ctx->graphs.size() >= 32) {  // evict the least recently used graph
-      auto victim = ctx->graphs.begin();
-      for (auto j = ctx->graphs.begin(); j != ctx->graphs.end(); ++j)
-        if (j->second.last_use < victim->second.last_use) victim = j;
-      cudaStreamSynchronize(ctx->stream);
-      destroy_graph(ctx, victim->second);
-      ctx->graphs.erase(victim);
-    }
-    GraphEntry entry;
-    cudaGraph_t graph = nullptr;
-    MAPI_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-    ctx->capturing = true;
-    ctx->capture_count = 0;
-    ctx->mark_sink = &entry.marks;
-    s = enqueue_solve(ctx, ctx->capture_stream, A, op, nvec, w0, ldw, max_iters, tol_l1, flags,
-                      w_out, ldw);
-    ctx->capturing = false;
-    ctx->mark_sink = nullptr;
-    entry.nodes = ctx->capture_count;
-    cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
-    if (s != MAPI_OK || e != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      destroy_graph(ctx, entry);
-      return s != MAPI_OK ? s : cuda_fail(ctx, e, "cudaStreamEndCapture");
-    }
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-      destroy_graph(ctx, entry);
-      return cuda_fail(ctx, e, "cudaGraphInstantiate");
-    }
-    entry.exec = exec;
-    entry.last_use = ++ctx->use_clock;
-    it = ctx->graphs.emplace(key, std::move(entry)).first;
-  }
-  MAPI_CUDA_TRY(ctx, cudaGraphLaunch(exec, ctx->stream));
-  ctx->stats.launches += it->second.nodes;
+  GraphEntry* ge = nullptr;
+  s = launch_cached_graph(
+      ctx, key,
+      [&](cudaStream_t cs) {
+        return enqueue_solve(ctx, cs, A, op, nvec, w0, ldw, max_iters, tol_l1, flags, w_out, ldw);
+      },
+      &ge);
+  if (s != MAPI_OK) return s;
   MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ctl_host, ctx->ctl.p, sizeof(IterCtl),
                                      cudaMemcpyDeviceToHost, ctx->stream));
   MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  prof_collect(ctx, it->second.marks, false);
-  prof_collect(ctx, ctx->pending, true);
+  finish_graph(ctx, ge);
   mapi_status result = MAPI_OK;
   for (int v = 0; v < nvec; ++v) {
     const VecState& st = ctx->ctl_host->v[v];

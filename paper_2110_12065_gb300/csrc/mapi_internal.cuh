@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <set>
@@ -108,6 +109,8 @@ struct mapi_ctx {
 
   // scratch for solves
   DevBuf ypart, wbuf0, wbuf1, ctl, aux, mcpart;
+  DevBuf pca_c0, pca_c1, pca_q, pca_defl;  // PCA scratch (covariances, deflation)
+  int* rec_host = nullptr;                 // pinned: per-component steps and statuses
   mapi::IterCtl* ctl_host = nullptr;  // pinned mirror of the control block
 
   // CUDA-graph cache: key -> executable graph
@@ -151,6 +154,15 @@ void prof_end(mapi_ctx* ctx, cudaStream_t s, cudaEvent_t a, int cls, double byte
 // Fold completed marks into the counters (stream already synchronised).
 void prof_collect(mapi_ctx* ctx, std::vector<ProfMark>& marks, bool recycle);
 void destroy_graph(mapi_ctx* ctx, GraphEntry& g);
+
+// Replay the CUDA graph cached under `key` on ctx->stream, capturing it from
+// `enqueue` (stream work only, no allocation) the first time.  The caller
+// synchronises and then calls finish_graph.
+mapi_status launch_cached_graph(mapi_ctx* ctx, const std::vector<int64_t>& key,
+                                const std::function<mapi_status(cudaStream_t)>& enqueue,
+                                GraphEntry** out);
+// After the stream has finished the replay: fold timings and launch counts.
+void finish_graph(mapi_ctx* ctx, GraphEntry* g);
 
 // Grow a scratch buffer (drops cached graphs when an address changes).
 mapi_status ensure(mapi_ctx* ctx, DevBuf& b, size_t bytes);

@@ -6,6 +6,7 @@
 #include <cudaTypedefs.h>
 
 #include <cmath>
+#include <cstring>
 
 #include "device_common.cuh"
 
@@ -293,6 +294,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
     else if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
   }
 }
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t local, unsigned rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+// 4-byte store into a peer CTA's shared memory that completes 4 bytes of the
+// transaction count of the peer's mbarrier.
+__device__ __forceinline__ void st_async_f32(uint32_t remote_addr, float v, uint32_t remote_bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(
+                   remote_addr),
+               "r"(__float_as_uint(v)), "r"(remote_bar)
+               : "memory");
+}
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
                                             uint64_t* bar) {
   asm volatile(
@@ -307,7 +321,7 @@ struct PairArgs {
   int ntiles;     // column tiles
   int nclusters;
   const float* w;  // current iterate (D entries + zero padding)
-  float* ypart;    // [nclusters][D_pad]
+  float* ypart;    // [D_pad][nclusters] (row-major by row)
   int D_pad;       // rows covered by one cluster (4 * 8 * RW)
   IterCtl* ctl;
 };
@@ -328,16 +342,19 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
   const int rbase = (int)crank * RC + warp * RW;  // first row of this warp
 
   extern __shared__ __align__(1024) uint32_t stage[];   // kPairStages x RC x 32 words
-  __shared__ __align__(8) uint64_t full[kPairStages];
+  __shared__ __align__(8) uint64_t full[kPairStages];   // TMA tile arrived
+  __shared__ __align__(8) uint64_t tready[2];           // all 4 column partials arrived
   __shared__ float4 wp[RC];                 // (lo, hi, s, 0) per row of this CTA
   __shared__ float tbuf[kPairWarps][TC];    // per-warp column partials
-  __shared__ float cpart[2][TC];            // CTA column partials (DSMEM-visible)
+  __shared__ float tin[2][kPairCluster][TC];  // column partials pushed by each CTA
   __shared__ int s_err;
 
   const int nmine = a.ntiles > cid ? (a.ntiles - cid + a.nclusters - 1) / a.nclusters : 0;
   if (threadIdx.x == 0) {
     s_err = 0;
     for (int s = 0; s < kPairStages; ++s) mbar_init(&full[s], 1);
+    mbar_init(&tready[0], 1);
+    mbar_init(&tready[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int r = threadIdx.x; r < RC; r += blockDim.x) {
@@ -356,6 +373,8 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
   };
   if (threadIdx.x == 0)
     for (int j = 0; j < nmine && j < kPairStages; ++j) issue(j);
+  // peers push into tin / tready only after the cluster has started
+  cluster.sync();
 
   float acc[RW];
 #pragma unroll
@@ -394,25 +413,31 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
       issue(j + kPairStages);
     }
     if (warp == 0) {
+      // CTA partial of this tile's columns, pushed to every CTA of the
+      // cluster (itself included); each push completes bytes of the
+      // receiver's tready[par]
+      if (lane == 0) mbar_expect_tx(&tready[par], kPairCluster * TC * 4);
+      __syncwarp();
 #pragma unroll
       for (int c = 0; c < CPL; ++c) {
         float sum = 0.f;
 #pragma unroll
         for (int w = 0; w < kPairWarps; ++w) sum += tbuf[w][lane * CPL + c];
-        cpart[par][lane * CPL + c] = sum;
+        const uint32_t loc = smem_u32(&tin[par][crank][lane * CPL + c]);
+        const uint32_t bar = smem_u32(&tready[par]);
+#pragma unroll
+        for (int q = 0; q < kPairCluster; ++q)
+          st_async_f32(mapa_u32(loc, q), sum, mapa_u32(bar, q));
       }
     }
-    cluster.sync();
+    if (!mbar_wait(&tready[par], (unsigned)((j >> 1) & 1))) s_err = 1;
     // t over the whole cluster, same order in every CTA
     typename Op<OP>::P tpar[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
       float t = 0.f;
 #pragma unroll
-      for (int r = 0; r < kPairCluster; ++r) {
-        const float* rem = cluster.map_shared_rank(&cpart[par][0], r);
-        t += rem[lane * CPL + c];
-      }
+      for (int r = 0; r < kPairCluster; ++r) t += tin[par][r][lane * CPL + c];
       tpar[c] = Op<OP>::prep(t);
     }
 #pragma unroll
@@ -429,7 +454,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
     float sum = acc[jj];
 #pragma unroll
     for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) a.ypart[(int64_t)cid * a.D_pad + rbase + jj] = sum;
+    if (lane == 0) a.ypart[(int64_t)(rbase + jj) * a.nclusters + cid] = sum;
   }
   if (threadIdx.x == 0 && s_err) {
     // a tile never arrived: report it; later kernels of the solve stop
@@ -437,8 +462,85 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
     a.ctl->v[0].done = 1;
     a.ctl->all_done = 1;
   }
-  cluster.sync();  // no CTA leaves while a peer may still read its cpart
+  cluster.sync();  // no CTA leaves while a peer may still push into it
 }
+
+// ======================================================================
+// Deflation of an iterate without forming Q.  For P = w (+) w^T with
+// c = |w|, s = sign(w) and z = s * y (min1):
+//   (P y)_i = s_i [ sum_{c_j <= c_i} c_j z_j + c_i sum_{c_j > c_i} z_j ],
+// which only needs w sorted by c: two prefix sums over the sorted order.
+// min2's outer product is half of (the min1 one + the same with every sign
+// +1); dot's is w (w . y).  k_defl_prep ranks one finished component once:
+// perm[p] = index at sorted position p, csort[p] = its c, ubi[i] = last
+// sorted position whose c is <= c_i (ties included).
+// ======================================================================
+constexpr int kDeflMaxD = 1024;
+
+__global__ void __launch_bounds__(kDeflMaxD) k_defl_prep(const float* __restrict__ w, int D,
+                                                        int* __restrict__ perm,
+                                                        float* __restrict__ csort,
+                                                        int* __restrict__ ubi) {
+  __shared__ float c[kDeflMaxD];
+  for (int i = threadIdx.x; i < D; i += blockDim.x) c[i] = fabsf(w[i]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < D; i += blockDim.x) {
+    const float ci = c[i];
+    int rank = 0, le = 0;
+    for (int j = 0; j < D; ++j) {
+      const float cj = c[j];
+      rank += (cj < ci) || (cj == ci && j < i);
+      le += (cj <= ci);
+    }
+    perm[rank] = i;
+    csort[rank] = ci;
+    ubi[i] = le - 1;
+  }
+}
+
+// In-place inclusive scan of x[0 .. 4*NT) in shared memory (fixed order).
+template <int NT>
+__device__ __forceinline__ void block_scan4(float* x, float* wtot) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  float v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = x[t * 4 + k];
+#pragma unroll
+  for (int k = 1; k < 4; ++k) v[k] += v[k - 1];
+  float incl = v[3];
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float n = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += n;
+  }
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    float wv = lane < NT / 32 ? wtot[lane] : 0.f;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float n = __shfl_up_sync(0xffffffffu, wv, o);
+      if (lane >= o) wv += n;
+    }
+    if (lane < NT / 32) wtot[lane] = wv;  // inclusive over warps
+  }
+  __syncthreads();
+  const float off = (incl - v[3]) + (warp > 0 ? wtot[warp - 1] : 0.f);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) x[t * 4 + k] = off + v[k];
+  __syncthreads();
+}
+
+struct DeflArgs {
+  int nprev;          // finished components to deflate (0: none)
+  int op;             // MAPI_OP_MIN1 / MIN2 / DOT
+  const float* P;     // components, column m at P + m * ldp
+  int64_t ldp;
+  const int* perm;    // [m][D_pad] per component (k_defl_prep)
+  const float* csort;
+  const int* ubi;
+  int64_t stride;     // elements between components in perm / csort / ubi
+};
 
 // ======================================================================
 // Pair-step finish: one cluster of CS CTAs.  CTA r owns rows [r*RS,
@@ -452,14 +554,31 @@ struct FinishArgs {
   const float* ypart;
   int nparts;
   int D, D_pad;
-  const float* Q;  // D x D (ld = ldq) or null
-  int64_t ldq;
+  DeflArgs defl;
   const float* w;
   float* w_next;
   IterCtl* ctl;
   int norm_l2;
   float denom;
 };
+
+// Sum over the cluster of one float per CTA (at `slot` in every CTA's shared
+// memory), read in parallel by the lanes of one warp and added in a fixed
+// butterfly order; every thread of the block gets the result.
+__device__ __forceinline__ float cluster_sum(cg::cluster_group& cluster, float* slot, int CS,
+                                             float* bcast) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    float v = lane < CS ? cluster.map_shared_rank(slot, lane)[0] : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) *bcast = v;
+  }
+  __syncthreads();
+  const float r = *bcast;
+  __syncthreads();
+  return r;
+}
 
 __global__ void __launch_bounds__(kFinThreads) k_pair_finish(FinishArgs a) {
   if (*(volatile int*)&a.ctl->all_done) return;
@@ -468,41 +587,179 @@ __global__ void __launch_bounds__(kFinThreads) k_pair_finish(FinishArgs a) {
   const int r = (int)cluster.block_rank();
   const int RS = a.D_pad / CS;
   const int r0 = r * RS;
+  constexpr int NW = kFinThreads / 32;
+  constexpr int PER = kDeflMaxD / kFinThreads;  // elements per thread over D <= 1024
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   extern __shared__ float fsh[];
-  float* ys = fsh;               // RS    own rows of y (read by peers)
-  float* u = fsh + RS;           // RS    own rows after deflation
-  float* yfull = fsh + 2 * RS;   // D_pad gathered y
+  float* ys = fsh;                    // RS    own rows of y (read by peers)
+  float* u = ys + RS;                 // RS    own rows after deflation
+  float* wo = u + RS;                 // RS    old iterate, own rows
+  float* yfull = wo + RS;             // D_pad gathered y
+  float* cbuf = yfull + a.D_pad;      // D_pad this CTA's sum of P_m y (read by peers)
+  float* sA = cbuf + a.D_pad;         // four scan buffers, kDeflMaxD each
+  float* sB = sA + kDeflMaxD;
+  float* sA2 = sB + kDeflMaxD;
+  float* sB2 = sA2 + kDeflMaxD;
+  float* wm_s = sB2 + kDeflMaxD;      // component m: w_m, sorted c, perm, ub
+  float* cs_s = wm_s + kDeflMaxD;
+  int* perm_s = reinterpret_cast<int*>(cs_s + kDeflMaxD);
+  int* ub_s = perm_s + kDeflMaxD;
   __shared__ float red[33];
-  __shared__ float part[4];      // [0] norm partial, [1] delta partial
+  __shared__ float part[4];      // [0] norm partial, [1] delta partial, [2..3] broadcasts
+  __shared__ float wtot[kFinThreads / 32];
+  __shared__ float dotv;
 
-  // 1. y for own rows: sum over partials in order; 4 threads per row
-  for (int i = threadIdx.x >> 2; i < RS; i += kFinThreads / 4) {
-    const int d = r0 + i;
-    float s = 0.f;
-    for (int g = (threadIdx.x & 3); g < a.nparts; g += 4) s += a.ypart[(int64_t)g * a.D_pad + d];
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    if ((threadIdx.x & 3) == 0) ys[i] = (d < a.D) ? s / a.denom : 0.f;
-  }
-  cluster.sync();
-  // 2. deflation u = y - Q y (needs the whole y)
-  if (a.Q) {
-    for (int i = threadIdx.x; i < a.D_pad; i += kFinThreads) {
-      const float* rem = cluster.map_shared_rank(ys, i / RS);
-      yfull[i] = rem[i % RS];
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i < RS; i += kFinThreads / 32) {
-      const int d = r0 + i;
-      float s = 0.f;
-      if (d < a.D) {
-        const float* qrow = a.Q + (int64_t)d * a.ldq;
-        for (int j = lane; j < a.D; j += 32) s = fmaf(qrow[j], yfull[j], s);
+  const int D = a.D;
+  const int m0 = r;  // first component of this CTA (products of m = r, r + CS, ...)
+  const bool mine = m0 < a.defl.nprev;
+  // 0. prefetch every global operand with independent loads (one round trip):
+  //    component m0's data, the old iterate's own rows, the cluster partials
+  if (mine) {
+    const float* wm = a.defl.P + (int64_t)m0 * a.defl.ldp;
+    if (a.defl.op == MAPI_OP_DOT) {
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x + k * kFinThreads;
+        if (i < D) wm_s[i] = wm[i];
+      }
+    } else {
+      const int* pg = a.defl.perm + (int64_t)m0 * a.defl.stride;
+      const float* cg_ = a.defl.csort + (int64_t)m0 * a.defl.stride;
+      const int* ug = a.defl.ubi + (int64_t)m0 * a.defl.stride;
+      float w_[PER], c_[PER];
+      int p_[PER], u_[PER];
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x + k * kFinThreads;
+        if (i < D) {
+          w_[k] = wm[i];
+          c_[k] = cg_[i];
+          p_[k] = pg[i];
+          u_[k] = ug[i];
+        }
       }
 #pragma unroll
-      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) u[i] = (d < a.D) ? ys[i] - s : 0.f;
+      for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x + k * kFinThreads;
+        if (i < D) {
+          wm_s[i] = w_[k];
+          cs_s[i] = c_[k];
+          perm_s[i] = p_[k];
+          ub_s[i] = u_[k];
+        }
+      }
+    }
+  }
+  for (int i = threadIdx.x; i < RS; i += kFinThreads) wo[i] = (r0 + i < D) ? a.w[r0 + i] : 0.f;
+  // 1. y for own rows: a warp per row, lanes over the (contiguous) cluster
+  //    partials, then a fixed butterfly; four rows in flight per warp
+  for (int i0 = warp * 4; i0 < RS; i0 += NW * 4) {
+    float sum[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sum[q] = 0.f;
+      const int i = i0 + q;
+      if (i < RS) {
+        const float* src = a.ypart + (int64_t)(r0 + i) * a.nparts;
+#pragma unroll 4
+        for (int g = lane; g < a.nparts; g += 32) sum[q] += src[g];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float v = sum[q];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      const int i = i0 + q;
+      if (lane == 0 && i < RS) ys[i] = (r0 + i < D) ? v / a.denom : 0.f;
+    }
+  }
+  cluster.sync();
+  // 2. deflation u = y - sum_m P_m y (prefix-sum form; all operands in smem)
+  if (a.defl.nprev > 0) {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * kFinThreads;
+      if (i < a.D_pad) yfull[i] = cluster.map_shared_rank(ys, i / RS)[i % RS];
+      if (i < a.D_pad) cbuf[i] = 0.f;
+    }
+    __syncthreads();
+    for (int m = m0; m < a.defl.nprev; m += CS) {
+      if (m != m0) {  // more components than CTAs: load this one (rare)
+        const float* wm = a.defl.P + (int64_t)m * a.defl.ldp;
+        for (int i = threadIdx.x; i < D; i += kFinThreads) {
+          wm_s[i] = wm[i];
+          if (a.defl.op != MAPI_OP_DOT) {
+            cs_s[i] = a.defl.csort[(int64_t)m * a.defl.stride + i];
+            perm_s[i] = a.defl.perm[(int64_t)m * a.defl.stride + i];
+            ub_s[i] = a.defl.ubi[(int64_t)m * a.defl.stride + i];
+          }
+        }
+        __syncthreads();
+      }
+      if (a.defl.op == MAPI_OP_DOT) {
+        Kahan kd;
+        for (int i = threadIdx.x; i < D; i += kFinThreads) kd.add(wm_s[i] * yfull[i]);
+        const float dv = block_sum<kFinThreads>(kd.value(), red);
+        if (threadIdx.x == 0) dotv = dv;
+        __syncthreads();
+        for (int i = threadIdx.x; i < D; i += kFinThreads) cbuf[i] += wm_s[i] * dotv;
+        __syncthreads();
+        continue;
+      }
+      const bool two = a.defl.op == MAPI_OP_MIN2;
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const int p = threadIdx.x + k * kFinThreads;
+        float z = 0.f, y = 0.f, c = 0.f;
+        if (p < D) {
+          const int i = perm_s[p];
+          y = yfull[i];
+          z = sgnf(wm_s[i]) * y;
+          c = cs_s[p];
+        }
+        sA[p] = c * z;
+        sB[p] = z;
+        if (two) {
+          sA2[p] = c * y;
+          sB2[p] = y;
+        }
+      }
+      __syncthreads();
+      block_scan4<kFinThreads>(sA, wtot);
+      block_scan4<kFinThreads>(sB, wtot);
+      if (two) {
+        block_scan4<kFinThreads>(sA2, wtot);
+        block_scan4<kFinThreads>(sB2, wtot);
+      }
+      const float totB = sB[D - 1], totB2 = two ? sB2[D - 1] : 0.f;
+      for (int i = threadIdx.x; i < D; i += kFinThreads) {
+        const float wi = wm_s[i], ci = fabsf(wi);
+        const int q = ub_s[i];
+        float v = sgnf(wi) * (sA[q] + ci * (totB - sB[q]));
+        if (two) v = 0.5f * (v + (sA2[q] + ci * (totB2 - sB2[q])));
+        cbuf[i] += v;
+      }
+      __syncthreads();
+    }
+    cluster.sync();
+    // own rows minus every CTA's products: lane q reads CTA q's value, a
+    // fixed butterfly adds them; four rows in flight per warp
+    const int nq = min(CS, a.defl.nprev);
+    for (int i0 = warp * 4; i0 < RS; i0 += NW * 4) {
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = i0 + e;
+        v[e] = (lane < nq && i < RS) ? cluster.map_shared_rank(cbuf, lane)[r0 + i] : 0.f;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
+        const int i = i0 + e;
+        if (lane == 0 && i < RS) u[i] = (r0 + i < D) ? ys[i] - v[e] : 0.f;
+      }
     }
     __syncthreads();
   } else {
@@ -518,35 +775,33 @@ __global__ void __launch_bounds__(kFinThreads) k_pair_finish(FinishArgs a) {
   const float np = block_sum<kFinThreads>(k.value(), red);
   if (threadIdx.x == 0) part[0] = np;
   cluster.sync();
-  float L = 0.f;
-  for (int q = 0; q < CS; ++q) L += cluster.map_shared_rank(part, q)[0];
+  float L = cluster_sum(cluster, &part[0], CS, &part[2]);
   if (a.norm_l2) L = sqrtf(L);
   const bool ok = (L > 0.f) && isfinite(L);
   Kahan dk;
   if (ok) {
     for (int i = threadIdx.x; i < RS; i += kFinThreads) {
       const int d = r0 + i;
-      if (d >= a.D) continue;
+      if (d >= D) continue;
       const float x = u[i] / L;
-      dk.add(fabsf(x - a.w[d]));
+      dk.add(fabsf(x - wo[i]));
       a.w_next[d] = x;
     }
   }
   const float dp = block_sum<kFinThreads>(dk.value(), red);
   if (threadIdx.x == 0) part[1] = dp;
   cluster.sync();
+  const float Dsum = (r == 0) ? cluster_sum(cluster, &part[1], CS, &part[3]) : 0.f;
   if (r == 0 && threadIdx.x == 0) {
     VecState* st = &a.ctl->v[0];
     if (!ok) {
       st->status = (L == 0.f) ? MAPI_EZERONORM : MAPI_ENONFINITE;
       st->done = 1;
     } else {
-      float D = 0.f;
-      for (int q = 0; q < CS; ++q) D += cluster.map_shared_rank(part, q)[1];
       st->iters += 1;
-      st->delta = D;
+      st->delta = Dsum;
       st->norm = L;
-      if (a.ctl->tol > 0.f && D < a.ctl->tol) st->done = 1;
+      if (a.ctl->tol > 0.f && Dsum < a.ctl->tol) st->done = 1;
     }
     a.ctl->all_done = st->done;
   }
@@ -715,6 +970,12 @@ static mapi_status plan_pair(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, PairL
   return MAPI_OK;
 }
 
+// ys, u, wo (own rows), yfull, cbuf (D_pad each), four scan buffers and the
+// component's w, sorted c, perm and ub (kDeflMaxD each)
+static size_t finish_smem(int D_pad, int cs) {
+  return (size_t)(3 * (D_pad / cs) + 2 * D_pad + 8 * kDeflMaxD) * sizeof(float);
+}
+
 static int finish_cluster_size(mapi_ctx* ctx, int D_pad) {
   static int cached = 0;
   if (cached) return cached;
@@ -728,7 +989,7 @@ static int finish_cluster_size(mapi_ctx* ctx, int D_pad) {
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(cs, 1, 1);
     cfg.blockDim = dim3(kFinThreads, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)(2 * (D_pad / cs) + D_pad) * sizeof(float);
+    cfg.dynamicSmemBytes = finish_smem(D_pad, cs);
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
@@ -744,7 +1005,7 @@ static int finish_cluster_size(mapi_ctx* ctx, int D_pad) {
 
 static mapi_status launch_pair_step(mapi_ctx* ctx, cudaStream_t s, const PairLaunch& pl,
                                     const mapi_mat* X, const float* w, float* w_next,
-                                    float* ypart, const float* Q, int64_t ldq, int fcs,
+                                    float* ypart, const DeflArgs& defl, int fcs,
                                     IterCtl* ctl, int norm_l2, float denom) {
   PairArgs pa;
   pa.D = X->rows;
@@ -780,8 +1041,7 @@ static mapi_status launch_pair_step(mapi_ctx* ctx, cudaStream_t s, const PairLau
   fa.nparts = pl.clusters;
   fa.D = X->rows;
   fa.D_pad = pa.D_pad;
-  fa.Q = Q;
-  fa.ldq = ldq;
+  fa.defl = defl;
   fa.w = w;
   fa.w_next = w_next;
   fa.ctl = ctl;
@@ -796,7 +1056,7 @@ static mapi_status launch_pair_step(mapi_ctx* ctx, cudaStream_t s, const PairLau
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(fcs, 1, 1);
     cfg.blockDim = dim3(kFinThreads, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)(2 * (pa.D_pad / fcs) + pa.D_pad) * sizeof(float);
+    cfg.dynamicSmemBytes = finish_smem(pa.D_pad, fcs);
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
@@ -808,153 +1068,199 @@ static mapi_status launch_pair_step(mapi_ctx* ctx, cudaStream_t s, const PairLau
   return MAPI_OK;
 }
 
-mapi_status run_pca(mapi_ctx* ctx, const mapi_mat* X, int k, int mode, mapi_op op,
-                    int iters, double tol, double denom, const float* w0, float* P_out,
-                    int* iters_done) {
-  const int D = X->rows;
-  cudaStream_t s = ctx->stream;
-  mapi_status st;
-  // device scratch: Q (D x D), two iterate buffers, counters
-  const int64_t ldq = (D + 3) / 4 * 4;
-  int* rec = nullptr;  // [iters k][status k]
-  if ((st = ensure(ctx, ctx->aux, 64 + sizeof(int) * 2 * 64 + 64)) != MAPI_OK) return st;
-  rec = (int*)((char*)ctx->aux.p + 64);
-  int* abort = rec + 128;
-  MAPI_CUDA_TRY(ctx, cudaMemsetAsync(rec, 0, sizeof(int) * 129, s));
+// Scratch of the min-covariance splits for X (the launcher grows it; callers
+// that capture graphs size it first).
+static size_t mincov_scratch_bytes(const mapi_ctx* ctx, const mapi_mat* X) {
+  const int T = (X->rows + kMcT - 1) / kMcT;
+  const int nt = T * (T + 1) / 2;
+  int nsplit = 1;
+  while (nt * nsplit < 4 * ctx->sm_count && X->ld / (nsplit * 2) >= 4 * kMcK) nsplit *= 2;
+  return sizeof(float) * (size_t)nsplit * nt * kMcT * kMcT;
+}
+
+namespace {
+
+// Everything one PCA solve touches on the device, sized before capture.
+struct PcaPlan {
+  int D = 0, k = 0, mode = 0, iters = 0;
+  mapi_op op = MAPI_OP_MIN1;
+  double tol = 0, denom = 1;
+  int64_t ldq = 0;
+  int* rec = nullptr;    // [iters 64][status 64][abort]
+  int* abort = nullptr;
+  // min-covariance mode
+  mapi_mat Cm, Ck;
   float* Q = nullptr;
-  DevBuf qbuf;
-  if (k > 1) {
-    if (cudaMalloc(&qbuf.p, sizeof(float) * D * ldq) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ctx, MAPI_ENOMEM, "deflation buffer");
-    }
-    Q = (float*)qbuf.p;
-  }
-  auto cleanup = [&]() {
-    if (qbuf.p) {
-      cudaStreamSynchronize(s);
-      cudaFree(qbuf.p);
-    }
-  };
-  const float fdenom = (float)denom;
-  if (mode == MAPI_PCA_MINCOV) {
-    // C and C_c live in internal F32 matrices so that the K1 path iterates them
-    mapi_mat Cm, Ck;
-    Cm.rows = Cm.cols = D;
-    Cm.rows_pad = (D + 63) / 64 * 64;
-    Cm.ld = ldq;
-    Cm.storage = MAPI_ST_F32;
-    Cm.owner = ctx;
-    Ck = Cm;
-    const size_t bytes = sizeof(float) * Cm.rows_pad * Cm.ld;
-    if (cudaMalloc(&Cm.data, bytes) != cudaSuccess || cudaMalloc(&Ck.data, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      if (Cm.data) cudaFree(Cm.data);
-      cleanup();
-      return fail(ctx, MAPI_ENOMEM, "covariance buffers");
-    }
-    auto free_c = [&]() {
-      cudaStreamSynchronize(s);
-      cudaFree(Cm.data);
-      cudaFree(Ck.data);
-    };
-    MAPI_CUDA_TRY(ctx, cudaMemsetAsync(Cm.data, 0, bytes, s));
-    MAPI_CUDA_TRY(ctx, cudaMemsetAsync(Ck.data, 0, bytes, s));
-    if ((st = launch_mincov_raw(ctx, X, op, fdenom, (float*)Cm.data, Cm.ld, s)) != MAPI_OK) {
-      free_c();
-      cleanup();
+  // pair mode
+  PairLaunch pl;
+  int D_pad = 0, fcs = 0;
+  int64_t wst = 0;
+  void* defl = nullptr;
+};
+
+mapi_status pca_enqueue(mapi_ctx* ctx, cudaStream_t s, const mapi_mat* X, const PcaPlan& p,
+                        const float* w0, float* P_out) {
+  mapi_status st = MAPI_OK;
+  const int D = p.D, k = p.k;
+  MAPI_CUDA_TRY(ctx, cudaMemsetAsync(p.rec, 0, sizeof(int) * 129, s));
+  if (p.mode == MAPI_PCA_MINCOV) {
+    const size_t bytes = sizeof(float) * p.Cm.rows_pad * p.Cm.ld;
+    MAPI_CUDA_TRY(ctx, cudaMemsetAsync(p.Cm.data, 0, bytes, s));
+    MAPI_CUDA_TRY(ctx, cudaMemsetAsync(p.Ck.data, 0, bytes, s));
+    if ((st = launch_mincov_raw(ctx, X, p.op, (float)p.denom, (float*)p.Cm.data, p.Cm.ld, s)) !=
+        MAPI_OK)
       return st;
-    }
-    if ((st = prepare_solve(ctx, &Cm, 1)) != MAPI_OK) {
-      free_c();
-      cleanup();
-      return st;
-    }
     for (int c = 0; c < k; ++c) {
-      const mapi_mat* A = &Cm;
+      const mapi_mat* A = &p.Cm;
       if (c > 0) {
-        if ((st = launch_build_Q(ctx, op, P_out, D, c, D, Q, ldq, s)) != MAPI_OK) break;
+        if ((st = launch_build_Q(ctx, p.op, P_out, D, c, D, p.Q, p.ldq, s)) != MAPI_OK) return st;
         dim3 g((D + 63) / 64, (D + 63) / 64);
-        k_deflate_gemm<<<g, 256, 0, s>>>((const float*)Cm.data, Q, D, ldq, (float*)Ck.data);
+        k_deflate_gemm<<<g, 256, 0, s>>>((const float*)p.Cm.data, p.Q, D, p.ldq,
+                                         (float*)p.Ck.data);
         MAPI_CUDA_TRY(ctx, cudaGetLastError());
         count_launch(ctx);
-        A = &Ck;
+        A = &p.Ck;
       }
-      if ((st = enqueue_solve(ctx, s, A, op, 1, w0 + (int64_t)c * D, D, iters, tol,
-                              MAPI_FLAG_FINAL_L2, P_out + (int64_t)c * D, D, abort)) != MAPI_OK)
-        break;
-      k_record<<<1, 1, 0, s>>>((const IterCtl*)ctx->ctl.p, rec, rec + 64, abort, c);
+      if ((st = enqueue_solve(ctx, s, A, p.op, 1, w0 + (int64_t)c * D, D, p.iters, p.tol,
+                              MAPI_FLAG_FINAL_L2, P_out + (int64_t)c * D, D, p.abort)) != MAPI_OK)
+        return st;
+      k_record<<<1, 1, 0, s>>>((const IterCtl*)ctx->ctl.p, p.rec, p.rec + 64, p.abort, c);
+      MAPI_CUDA_TRY(ctx, cudaGetLastError());
       count_launch(ctx);
     }
-    free_c();
-  } else if (mode == MAPI_PCA_PAIR) {
-    PairLaunch pl;
-    if ((st = plan_pair(ctx, X, op, &pl)) != MAPI_OK) {
-      cleanup();
-      return st;
-    }
-    const int D_pad = kPairCluster * kPairWarps * pl.rw;
-    const int fcs = finish_cluster_size(ctx, D_pad);
-    // every warp of the finish kernel covers 8 whole rows per pass
-    if (fcs && (D_pad / fcs) % 8 != 0) {
-      cleanup();
-      return fail(ctx, MAPI_EINVAL, "unsupported pair-mode row count");
-    }
-    if (!fcs) {
-      cleanup();
-      return fail(ctx, MAPI_ECUDA, "finish kernel: no cluster fits");
-    }
-    const int64_t wst = (D_pad + 15) / 16 * 16;
-    if ((st = ensure(ctx, ctx->wbuf0, sizeof(float) * wst)) != MAPI_OK ||
-        (st = ensure(ctx, ctx->wbuf1, sizeof(float) * wst)) != MAPI_OK ||
-        (st = ensure(ctx, ctx->ypart, sizeof(float) * (size_t)pl.clusters * D_pad)) != MAPI_OK ||
-        (st = ensure(ctx, ctx->ctl, sizeof(IterCtl))) != MAPI_OK) {
-      cleanup();
-      return st;
-    }
-    float* wb0 = (float*)ctx->wbuf0.p;
-    float* wb1 = (float*)ctx->wbuf1.p;
-    IterCtl* ctl = (IterCtl*)ctx->ctl.p;
-    const int norm_l2 = (op == MAPI_OP_DOT) ? 1 : 0;
-    for (int c = 0; c < k; ++c) {
-      if (c > 0) {
-        if ((st = launch_build_Q(ctx, op, P_out, D, c, D, Q, ldq, s)) != MAPI_OK) break;
-      }
-      if ((st = launch_start_float(ctx, s, w0 + (int64_t)c * D, D, D, 1, wb0, wb1, wst, 0, ctl,
-                                   (float)tol, abort)) != MAPI_OK)
-        break;
-      for (int t = 0; t < iters; ++t) {
-        const float* wc = (t & 1) ? wb1 : wb0;
-        float* wn = (t & 1) ? wb0 : wb1;
-        if ((st = launch_pair_step(ctx, s, pl, X, wc, wn, (float*)ctx->ypart.p,
-                                   c > 0 ? Q : nullptr, ldq, fcs, ctl, norm_l2, fdenom)) !=
-            MAPI_OK)
-          break;
-      }
-      if (st != MAPI_OK) break;
-      if ((st = launch_finish(ctx, s, wb0, wb1, wst, D, 1, ctl, 1, 0, 0,
-                              P_out + (int64_t)c * D, D)) != MAPI_OK)
-        break;
-      k_record<<<1, 1, 0, s>>>(ctl, rec, rec + 64, abort, c);
+    return MAPI_OK;
+  }
+  // pair mode
+  float* wb0 = (float*)ctx->wbuf0.p;
+  float* wb1 = (float*)ctx->wbuf1.p;
+  IterCtl* ctl = (IterCtl*)ctx->ctl.p;
+  const int norm_l2 = (p.op == MAPI_OP_DOT) ? 1 : 0;
+  int* perm = (int*)p.defl;
+  float* csort = (float*)((int*)p.defl + (size_t)k * p.D_pad);
+  int* ubi = (int*)p.defl + 2 * (size_t)k * p.D_pad;
+  DeflArgs defl{};
+  defl.op = p.op;
+  defl.P = P_out;
+  defl.ldp = D;
+  defl.stride = p.D_pad;
+  defl.perm = perm;
+  defl.csort = csort;
+  defl.ubi = ubi;
+  for (int c = 0; c < k; ++c) {
+    if (c > 0 && p.op != MAPI_OP_DOT) {
+      const size_t o = (size_t)(c - 1) * p.D_pad;
+      k_defl_prep<<<1, kDeflMaxD, 0, s>>>(P_out + (int64_t)(c - 1) * D, D, perm + o, csort + o,
+                                         ubi + o);
+      MAPI_CUDA_TRY(ctx, cudaGetLastError());
       count_launch(ctx);
     }
-  } else {
-    cleanup();
+    defl.nprev = c;
+    if ((st = launch_start_float(ctx, s, w0 + (int64_t)c * D, D, D, 1, wb0, wb1, p.wst, 0, ctl,
+                                 (float)p.tol, p.abort)) != MAPI_OK)
+      return st;
+    for (int t = 0; t < p.iters; ++t) {
+      const float* wc = (t & 1) ? wb1 : wb0;
+      float* wn = (t & 1) ? wb0 : wb1;
+      if ((st = launch_pair_step(ctx, s, p.pl, X, wc, wn, (float*)ctx->ypart.p, defl, p.fcs, ctl,
+                                 norm_l2, (float)p.denom)) != MAPI_OK)
+        return st;
+    }
+    if ((st = launch_finish(ctx, s, wb0, wb1, p.wst, D, 1, ctl, 1, 0, 0, P_out + (int64_t)c * D,
+                            D)) != MAPI_OK)
+      return st;
+    k_record<<<1, 1, 0, s>>>(ctl, p.rec, p.rec + 64, p.abort, c);
+    MAPI_CUDA_TRY(ctx, cudaGetLastError());
+    count_launch(ctx);
+  }
+  return MAPI_OK;
+}
+
+}  // namespace
+
+mapi_status run_pca(mapi_ctx* ctx, const mapi_mat* X, int k, int mode, mapi_op op, int iters,
+                    double tol, double denom, const float* w0, float* P_out, int* iters_done) {
+  if (mode != MAPI_PCA_MINCOV && mode != MAPI_PCA_PAIR)
     return fail(ctx, MAPI_EINVAL, "mode must be MINCOV or PAIR");
+  PcaPlan p;
+  p.D = X->rows;
+  p.k = k;
+  p.mode = mode;
+  p.op = op;
+  p.iters = iters;
+  p.tol = tol;
+  p.denom = denom;
+  p.ldq = (p.D + 3) / 4 * 4;
+  mapi_status st;
+  // ---- every allocation happens here, before any capture
+  if ((st = ensure(ctx, ctx->aux, 64 + sizeof(int) * 129)) != MAPI_OK) return st;
+  if (mode == MAPI_PCA_MINCOV) {
+    p.Cm.rows = p.Cm.cols = p.D;
+    p.Cm.rows_pad = (p.D + 63) / 64 * 64;
+    p.Cm.ld = p.ldq;
+    p.Cm.storage = MAPI_ST_F32;
+    p.Cm.owner = ctx;
+    p.Ck = p.Cm;
+    const size_t bytes = sizeof(float) * p.Cm.rows_pad * p.Cm.ld;
+    if ((st = ensure(ctx, ctx->pca_c0, bytes)) != MAPI_OK ||
+        (st = ensure(ctx, ctx->pca_c1, bytes)) != MAPI_OK ||
+        (st = ensure(ctx, ctx->mcpart, mincov_scratch_bytes(ctx, X))) != MAPI_OK)
+      return st;
+    if (k > 1 && (st = ensure(ctx, ctx->pca_q, sizeof(float) * p.D * p.ldq)) != MAPI_OK) return st;
+    if ((st = prepare_solve(ctx, &p.Cm, 1)) != MAPI_OK) return st;
+  } else {
+    if ((st = plan_pair(ctx, X, op, &p.pl)) != MAPI_OK) return st;
+    p.D_pad = kPairCluster * kPairWarps * p.pl.rw;
+    p.fcs = finish_cluster_size(ctx, p.D_pad);
+    if (!p.fcs) return fail(ctx, MAPI_ECUDA, "finish kernel: no cluster fits");
+    if ((p.D_pad / p.fcs) % 8 != 0) return fail(ctx, MAPI_EINVAL, "unsupported pair-mode row count");
+    p.wst = (p.D_pad + 15) / 16 * 16;
+    if ((st = ensure(ctx, ctx->wbuf0, sizeof(float) * p.wst)) != MAPI_OK ||
+        (st = ensure(ctx, ctx->wbuf1, sizeof(float) * p.wst)) != MAPI_OK ||
+        (st = ensure(ctx, ctx->ypart, sizeof(float) * (size_t)p.pl.clusters * p.D_pad)) != MAPI_OK ||
+        (st = ensure(ctx, ctx->ctl, sizeof(IterCtl))) != MAPI_OK ||
+        (st = ensure(ctx, ctx->pca_defl, sizeof(int) * 3 * (size_t)k * p.D_pad)) != MAPI_OK)
+      return st;
   }
-  if (st != MAPI_OK) {
-    cleanup();
-    return st;
-  }
-  int host[128];
-  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(host, rec, sizeof(int) * 128, cudaMemcpyDeviceToHost, s));
-  MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-  prof_collect(ctx, ctx->pending, true);
-  cleanup();
+  // addresses are final now (ensure may have moved buffers and dropped graphs)
+  p.rec = (int*)((char*)ctx->aux.p + 64);
+  p.abort = p.rec + 128;
+  p.Cm.data = ctx->pca_c0.p;
+  p.Ck.data = ctx->pca_c1.p;
+  p.Q = (float*)ctx->pca_q.p;
+  p.defl = ctx->pca_defl.p;
+
+  uint64_t tb, db;
+  std::memcpy(&tb, &tol, 8);
+  std::memcpy(&db, &denom, 8);
+  std::vector<int64_t> key = {2,
+                              (int64_t)X->id,
+                              k,
+                              mode,
+                              (int64_t)op,
+                              iters,
+                              (int64_t)tb,
+                              (int64_t)db,
+                              (int64_t)(uintptr_t)w0,
+                              (int64_t)(uintptr_t)P_out,
+                              (int64_t)ctx->prof_on,
+                              (int64_t)(uintptr_t)ctx->aux.p,
+                              (int64_t)(uintptr_t)ctx->wbuf0.p,
+                              (int64_t)(uintptr_t)ctx->ypart.p,
+                              (int64_t)(uintptr_t)ctx->pca_c0.p,
+                              (int64_t)(uintptr_t)ctx->pca_defl.p};
+  GraphEntry* ge = nullptr;
+  st = launch_cached_graph(
+      ctx, key, [&](cudaStream_t cs) { return pca_enqueue(ctx, cs, X, p, w0, P_out); }, &ge);
+  if (st != MAPI_OK) return st;
+  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->rec_host, p.rec, sizeof(int) * 128,
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+  MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  finish_graph(ctx, ge);
   mapi_status result = MAPI_OK;
   for (int c = 0; c < k; ++c) {
-    if (iters_done) iters_done[c] = host[c];
-    if (result == MAPI_OK && host[64 + c] != MAPI_OK) result = (mapi_status)host[64 + c];
+    if (iters_done) iters_done[c] = ctx->rec_host[c];
+    if (result == MAPI_OK && ctx->rec_host[64 + c] != MAPI_OK)
+      result = (mapi_status)ctx->rec_host[64 + c];
   }
   if (result != MAPI_OK) fail(ctx, result, "a component stopped early with this status");
   return result;
