@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -226,6 +227,83 @@ __global__ void __launch_bounds__(256)
 }
 
 // ======================================================================
+// Deflation of an iterate without forming Q.  For P = w (+) w^T with
+// c = |w|, s = sign(w) and z = s * y (min1):
+//   (P y)_i = s_i [ sum_{c_j <= c_i} c_j z_j + c_i sum_{c_j > c_i} z_j ],
+// which only needs w sorted by c: two prefix sums over the sorted order.
+// min2's outer product is half of (the min1 one + the same with every sign
+// +1); dot's is w (w . y).  k_defl_prep ranks one finished component once:
+// perm[p] = index at sorted position p, csort[p] = its c, ubi[i] = last
+// sorted position whose c is <= c_i (ties included).
+// ======================================================================
+constexpr int kDeflMaxD = 1024;
+
+__global__ void __launch_bounds__(kDeflMaxD) k_defl_prep(const float* __restrict__ w, int D,
+                                                        int* __restrict__ perm,
+                                                        float* __restrict__ csort,
+                                                        int* __restrict__ ubi) {
+  __shared__ float c[kDeflMaxD];
+  for (int i = threadIdx.x; i < D; i += blockDim.x) c[i] = fabsf(w[i]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < D; i += blockDim.x) {
+    const float ci = c[i];
+    int rank = 0, le = 0;
+    for (int j = 0; j < D; ++j) {
+      const float cj = c[j];
+      rank += (cj < ci) || (cj == ci && j < i);
+      le += (cj <= ci);
+    }
+    perm[rank] = i;
+    csort[rank] = ci;
+    ubi[i] = le - 1;
+  }
+}
+
+// In-place inclusive scan of x[0 .. 4*NT) in shared memory (fixed order).
+template <int NT>
+__device__ __forceinline__ void block_scan4(float* x, float* wtot) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  float v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = x[t * 4 + k];
+#pragma unroll
+  for (int k = 1; k < 4; ++k) v[k] += v[k - 1];
+  float incl = v[3];
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float n = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += n;
+  }
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    float wv = lane < NT / 32 ? wtot[lane] : 0.f;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float n = __shfl_up_sync(0xffffffffu, wv, o);
+      if (lane >= o) wv += n;
+    }
+    if (lane < NT / 32) wtot[lane] = wv;  // inclusive over warps
+  }
+  __syncthreads();
+  const float off = (incl - v[3]) + (warp > 0 ? wtot[warp - 1] : 0.f);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) x[t * 4 + k] = off + v[k];
+  __syncthreads();
+}
+
+struct DeflArgs {
+  int nprev;          // finished components to deflate (0: none)
+  int op;             // MAPI_OP_MIN1 / MIN2 / DOT
+  const float* P;     // components, column m at P + m * ldp
+  int64_t ldp;
+  const int* perm;    // [m][D_pad] per component (k_defl_prep)
+  const float* csort;
+  const int* ubi;
+  int64_t stride;     // elements between components in perm / csort / ubi
+};
+
+// ======================================================================
 // K4: pair step partials.  A cluster of 4 CTAs owns a stream of column
 // tiles of X; CTA r of the cluster holds rows [r*RC, (r+1)*RC) of each tile
 // (RC = 8 warps x RW rows).  Tiles arrive in shared memory through a
@@ -316,252 +394,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-struct PairArgs {
-  int D;          // logical rows
-  int ntiles;     // column tiles
-  int nclusters;
-  const float* w;  // current iterate (D entries + zero padding)
-  float* ypart;    // [D_pad][nclusters] (row-major by row)
-  int D_pad;       // rows covered by one cluster (4 * 8 * RW)
-  IterCtl* ctl;
-};
-
-template <int OP, int ST, int RW>
-__global__ void __launch_bounds__(kPairWarps * 32, 2)
-    k_pair_partial(const __grid_constant__ CUtensorMap xmap, PairArgs a) {
-  if (*(volatile const int*)&a.ctl->all_done) return;
-  using PC = PairCols<ST>;
-  constexpr int CPL = PC::CPL;
-  constexpr int TC = 32 * CPL;   // columns per tile
-  constexpr int RC = kPairWarps * RW;
-  constexpr unsigned kStageBytes = RC * 128;
-  cg::cluster_group cluster = cg::this_cluster();
-  const unsigned crank = cluster.block_rank();
-  const int cid = blockIdx.x / kPairCluster;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rbase = (int)crank * RC + warp * RW;  // first row of this warp
-
-  extern __shared__ __align__(1024) uint32_t stage[];   // kPairStages x RC x 32 words
-  __shared__ __align__(8) uint64_t full[kPairStages];   // TMA tile arrived
-  __shared__ __align__(8) uint64_t tready[2];           // all 4 column partials arrived
-  __shared__ float4 wp[RC];                 // (lo, hi, s, 0) per row of this CTA
-  __shared__ float tbuf[kPairWarps][TC];    // per-warp column partials
-  __shared__ float tin[2][kPairCluster][TC];  // column partials pushed by each CTA
-  __shared__ int s_err;
-
-  const int nmine = a.ntiles > cid ? (a.ntiles - cid + a.nclusters - 1) / a.nclusters : 0;
-  if (threadIdx.x == 0) {
-    s_err = 0;
-    for (int s = 0; s < kPairStages; ++s) mbar_init(&full[s], 1);
-    mbar_init(&tready[0], 1);
-    mbar_init(&tready[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  for (int r = threadIdx.x; r < RC; r += blockDim.x) {
-    const int d = (int)crank * RC + r;
-    const float wv = d < a.D ? a.w[d] : 0.f;
-    const auto p = Op<OP>::prep(wv);
-    if constexpr (OP == MAPI_OP_DOT) wp[r] = make_float4(p.w, 0.f, 0.f, 0.f);
-    else wp[r] = make_float4(p.lo, p.hi, p.s, 0.f);
-  }
-  __syncthreads();
-  auto issue = [&](int j) {
-    const int s = j % kPairStages;
-    const int tile = cid + j * a.nclusters;
-    mbar_expect_tx(&full[s], kStageBytes);
-    tma_load_2d(stage + (size_t)s * RC * 32, &xmap, tile * TC, (int)crank * RC, &full[s]);
-  };
-  if (threadIdx.x == 0)
-    for (int j = 0; j < nmine && j < kPairStages; ++j) issue(j);
-  // peers push into tin / tready only after the cluster has started
-  cluster.sync();
-
-  float acc[RW];
-#pragma unroll
-  for (int j = 0; j < RW; ++j) acc[j] = 0.f;
-
-  for (int j = 0; j < nmine; ++j) {
-    const int s = j % kPairStages;
-    const int par = j & 1;
-    const bool ok = mbar_wait(&full[s], (unsigned)((j / kPairStages) & 1));
-    if (!ok) s_err = 1;
-    uint32_t raw[RW];
-    const uint32_t* src = stage + (size_t)s * RC * 32 + (size_t)(warp * RW) * 32 + lane;
-#pragma unroll
-    for (int jj = 0; jj < RW; ++jj) raw[jj] = src[jj * 32];
-    // column partials over this warp's rows
-    float tp[CPL];
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) tp[c] = 0.f;
-#pragma unroll
-    for (int jj = 0; jj < RW; ++jj) {
-      float x[CPL];
-      PC::get(raw[jj], x);
-      const float4 q = wp[warp * RW + jj];
-      typename Op<OP>::P p;
-      if constexpr (OP == MAPI_OP_DOT) p = {q.x};
-      else p = {q.x, q.y, q.z};
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) tp[c] = Op<OP>::term(x[c], p, tp[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) tbuf[warp][lane * CPL + c] = tp[c];
-    __syncthreads();
-    // every warp has read stage s: refill it with tile j + S
-    if (threadIdx.x == 0 && j + kPairStages < nmine && !s_err) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(j + kPairStages);
-    }
-    if (warp == 0) {
-      // CTA partial of this tile's columns, pushed to every CTA of the
-      // cluster (itself included); each push completes bytes of the
-      // receiver's tready[par]
-      if (lane == 0) mbar_expect_tx(&tready[par], kPairCluster * TC * 4);
-      __syncwarp();
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        float sum = 0.f;
-#pragma unroll
-        for (int w = 0; w < kPairWarps; ++w) sum += tbuf[w][lane * CPL + c];
-        const uint32_t loc = smem_u32(&tin[par][crank][lane * CPL + c]);
-        const uint32_t bar = smem_u32(&tready[par]);
-#pragma unroll
-        for (int q = 0; q < kPairCluster; ++q)
-          st_async_f32(mapa_u32(loc, q), sum, mapa_u32(bar, q));
-      }
-    }
-    if (!mbar_wait(&tready[par], (unsigned)((j >> 1) & 1))) s_err = 1;
-    // t over the whole cluster, same order in every CTA
-    typename Op<OP>::P tpar[CPL];
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-      float t = 0.f;
-#pragma unroll
-      for (int r = 0; r < kPairCluster; ++r) t += tin[par][r][lane * CPL + c];
-      tpar[c] = Op<OP>::prep(t);
-    }
-#pragma unroll
-    for (int jj = 0; jj < RW; ++jj) {
-      float x[CPL];
-      PC::get(raw[jj], x);
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) acc[jj] = Op<OP>::term(x[c], tpar[c], acc[jj]);
-    }
-  }
-  // row sums across the 32 lanes, written once per cluster
-#pragma unroll
-  for (int jj = 0; jj < RW; ++jj) {
-    float sum = acc[jj];
-#pragma unroll
-    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) a.ypart[(int64_t)(rbase + jj) * a.nclusters + cid] = sum;
-  }
-  if (threadIdx.x == 0 && s_err) {
-    // a tile never arrived: report it; later kernels of the solve stop
-    a.ctl->v[0].status = MAPI_ETIMEOUT;
-    a.ctl->v[0].done = 1;
-    a.ctl->all_done = 1;
-  }
-  cluster.sync();  // no CTA leaves while a peer may still push into it
-}
-
-// ======================================================================
-// Deflation of an iterate without forming Q.  For P = w (+) w^T with
-// c = |w|, s = sign(w) and z = s * y (min1):
-//   (P y)_i = s_i [ sum_{c_j <= c_i} c_j z_j + c_i sum_{c_j > c_i} z_j ],
-// which only needs w sorted by c: two prefix sums over the sorted order.
-// min2's outer product is half of (the min1 one + the same with every sign
-// +1); dot's is w (w . y).  k_defl_prep ranks one finished component once:
-// perm[p] = index at sorted position p, csort[p] = its c, ubi[i] = last
-// sorted position whose c is <= c_i (ties included).
-// ======================================================================
-constexpr int kDeflMaxD = 1024;
-
-__global__ void __launch_bounds__(kDeflMaxD) k_defl_prep(const float* __restrict__ w, int D,
-                                                        int* __restrict__ perm,
-                                                        float* __restrict__ csort,
-                                                        int* __restrict__ ubi) {
-  __shared__ float c[kDeflMaxD];
-  for (int i = threadIdx.x; i < D; i += blockDim.x) c[i] = fabsf(w[i]);
-  __syncthreads();
-  for (int i = threadIdx.x; i < D; i += blockDim.x) {
-    const float ci = c[i];
-    int rank = 0, le = 0;
-    for (int j = 0; j < D; ++j) {
-      const float cj = c[j];
-      rank += (cj < ci) || (cj == ci && j < i);
-      le += (cj <= ci);
-    }
-    perm[rank] = i;
-    csort[rank] = ci;
-    ubi[i] = le - 1;
-  }
-}
-
-// In-place inclusive scan of x[0 .. 4*NT) in shared memory (fixed order).
-template <int NT>
-__device__ __forceinline__ void block_scan4(float* x, float* wtot) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  float v[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) v[k] = x[t * 4 + k];
-#pragma unroll
-  for (int k = 1; k < 4; ++k) v[k] += v[k - 1];
-  float incl = v[3];
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float n = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += n;
-  }
-  if (lane == 31) wtot[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    float wv = lane < NT / 32 ? wtot[lane] : 0.f;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const float n = __shfl_up_sync(0xffffffffu, wv, o);
-      if (lane >= o) wv += n;
-    }
-    if (lane < NT / 32) wtot[lane] = wv;  // inclusive over warps
-  }
-  __syncthreads();
-  const float off = (incl - v[3]) + (warp > 0 ? wtot[warp - 1] : 0.f);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) x[t * 4 + k] = off + v[k];
-  __syncthreads();
-}
-
-struct DeflArgs {
-  int nprev;          // finished components to deflate (0: none)
-  int op;             // MAPI_OP_MIN1 / MIN2 / DOT
-  const float* P;     // components, column m at P + m * ldp
-  int64_t ldp;
-  const int* perm;    // [m][D_pad] per component (k_defl_prep)
-  const float* csort;
-  const int* ubi;
-  int64_t stride;     // elements between components in perm / csort / ubi
-};
-
-// ======================================================================
-// Pair-step finish: one cluster of CS CTAs.  CTA r owns rows [r*RS,
-// (r+1)*RS): it reduces the cluster partials (fixed order), deflates
-// u = y - Q y (Q dense, optional), and after a cluster-wide norm normalises
-// w_next = u / ||u||_1 (||u||_2 for DOT), computes delta and the stop test.
-// ======================================================================
-constexpr int kFinThreads = 256;
-
-struct FinishArgs {
-  const float* ypart;
-  int nparts;
-  int D, D_pad;
-  DeflArgs defl;
-  const float* w;
-  float* w_next;
-  IterCtl* ctl;
-  int norm_l2;
-  float denom;
-};
-
 // Sum over the cluster of one float per CTA (at `slot` in every CTA's shared
 // memory), read in parallel by the lanes of one warp and added in a fixed
 // butterfly order; every thread of the block gets the result.
@@ -580,69 +412,84 @@ __device__ __forceinline__ float cluster_sum(cg::cluster_group& cluster, float* 
   return r;
 }
 
-__global__ void __launch_bounds__(kFinThreads) k_pair_finish(FinishArgs a) {
-  if (*(volatile int*)&a.ctl->all_done) return;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int CS = (int)cluster.num_blocks();
+struct PairArgs {
+  int D;          // logical rows
+  int ntiles;     // column tiles
+  int nclusters;
+  const float* w;  // current iterate (D entries + zero padding)
+  float* w_next;   // next iterate (written by the last cluster)
+  float* ypart;    // [D_pad][pstride] partial row sums, one column per cluster
+  int pstride;     // nclusters rounded up to a multiple of 4
+  int D_pad;       // rows covered by one cluster (4 * 8 * RW)
+  IterCtl* ctl;
+  DeflArgs defl;
+  int norm_l2;
+  float denom;
+};
+
+// Floats of shared memory the last cluster's epilogue needs: ys, u, wo (own
+// rows), yfull and cbuf (D_pad each), four scan buffers and the component's
+// w, sorted c, perm and ub (kDeflMaxD each).
+__host__ __device__ constexpr int pair_epi_floats(int rc, int d_pad) {
+  return 3 * rc + 2 * d_pad + 8 * kDeflMaxD;
+}
+
+// Epilogue of one pair step, run by the last cluster to finish: CTA r owns
+// rows [r*RS, (r+1)*RS) (the rows it streamed).  y = sum of the cluster
+// partials (fixed order) / denom; u = y - sum_m P_m y (prefix-sum form,
+// components spread over the 4 CTAs); w_next = u / ||u||_1 (||u||_2 for
+// DOT); delta and the stop test.  Shared memory: the (now idle) stage ring.
+template <int RS>
+__device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, float* fsh) {
+  constexpr int CS = kPairCluster;
+  constexpr int NT = kPairWarps * 32;
+  constexpr int PER = kDeflMaxD / NT;
   const int r = (int)cluster.block_rank();
-  const int RS = a.D_pad / CS;
   const int r0 = r * RS;
-  constexpr int NW = kFinThreads / 32;
-  constexpr int PER = kDeflMaxD / kFinThreads;  // elements per thread over D <= 1024
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  extern __shared__ float fsh[];
-  float* ys = fsh;                    // RS    own rows of y (read by peers)
-  float* u = ys + RS;                 // RS    own rows after deflation
-  float* wo = u + RS;                 // RS    old iterate, own rows
-  float* yfull = wo + RS;             // D_pad gathered y
-  float* cbuf = yfull + a.D_pad;      // D_pad this CTA's sum of P_m y (read by peers)
-  float* sA = cbuf + a.D_pad;         // four scan buffers, kDeflMaxD each
+  const int D = a.D;
+  float* ys = fsh;
+  float* u = ys + RS;
+  float* wo = u + RS;
+  float* yfull = wo + RS;
+  float* cbuf = yfull + a.D_pad;
+  float* sA = cbuf + a.D_pad;
   float* sB = sA + kDeflMaxD;
   float* sA2 = sB + kDeflMaxD;
   float* sB2 = sA2 + kDeflMaxD;
-  float* wm_s = sB2 + kDeflMaxD;      // component m: w_m, sorted c, perm, ub
+  float* wm_s = sB2 + kDeflMaxD;
   float* cs_s = wm_s + kDeflMaxD;
   int* perm_s = reinterpret_cast<int*>(cs_s + kDeflMaxD);
   int* ub_s = perm_s + kDeflMaxD;
   __shared__ float red[33];
-  __shared__ float part[4];      // [0] norm partial, [1] delta partial, [2..3] broadcasts
-  __shared__ float wtot[kFinThreads / 32];
+  __shared__ float part[4];
+  __shared__ float wtot[NT / 32];
   __shared__ float dotv;
 
-  const int D = a.D;
-  const int m0 = r;  // first component of this CTA (products of m = r, r + CS, ...)
-  const bool mine = m0 < a.defl.nprev;
-  // 0. prefetch every global operand with independent loads (one round trip):
-  //    component m0's data, the old iterate's own rows, the cluster partials
-  if (mine) {
+  // 0. prefetch: this CTA's first component, the old iterate's own rows
+  const int m0 = r;
+  if (m0 < a.defl.nprev) {
     const float* wm = a.defl.P + (int64_t)m0 * a.defl.ldp;
-    if (a.defl.op == MAPI_OP_DOT) {
+    const bool dot = a.defl.op == MAPI_OP_DOT;
+    float w_[PER], c_[PER];
+    int p_[PER], u_[PER];
 #pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const int i = threadIdx.x + k * kFinThreads;
-        if (i < D) wm_s[i] = wm[i];
-      }
-    } else {
-      const int* pg = a.defl.perm + (int64_t)m0 * a.defl.stride;
-      const float* cg_ = a.defl.csort + (int64_t)m0 * a.defl.stride;
-      const int* ug = a.defl.ubi + (int64_t)m0 * a.defl.stride;
-      float w_[PER], c_[PER];
-      int p_[PER], u_[PER];
-#pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const int i = threadIdx.x + k * kFinThreads;
-        if (i < D) {
-          w_[k] = wm[i];
-          c_[k] = cg_[i];
-          p_[k] = pg[i];
-          u_[k] = ug[i];
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < D) {
+        w_[k] = wm[i];
+        if (!dot) {
+          c_[k] = a.defl.csort[(int64_t)m0 * a.defl.stride + i];
+          p_[k] = a.defl.perm[(int64_t)m0 * a.defl.stride + i];
+          u_[k] = a.defl.ubi[(int64_t)m0 * a.defl.stride + i];
         }
       }
+    }
 #pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const int i = threadIdx.x + k * kFinThreads;
-        if (i < D) {
-          wm_s[i] = w_[k];
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < D) {
+        wm_s[i] = w_[k];
+        if (!dot) {
           cs_s[i] = c_[k];
           perm_s[i] = p_[k];
           ub_s[i] = u_[k];
@@ -650,44 +497,40 @@ __global__ void __launch_bounds__(kFinThreads) k_pair_finish(FinishArgs a) {
       }
     }
   }
-  for (int i = threadIdx.x; i < RS; i += kFinThreads) wo[i] = (r0 + i < D) ? a.w[r0 + i] : 0.f;
-  // 1. y for own rows: a warp per row, lanes over the (contiguous) cluster
-  //    partials, then a fixed butterfly; four rows in flight per warp
-  for (int i0 = warp * 4; i0 < RS; i0 += NW * 4) {
-    float sum[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      sum[q] = 0.f;
-      const int i = i0 + q;
-      if (i < RS) {
-        const float* src = a.ypart + (int64_t)(r0 + i) * a.nparts;
-#pragma unroll 4
-        for (int g = lane; g < a.nparts; g += 32) sum[q] += src[g];
-      }
+  // 1. own rows of y: one row per thread, the row's cluster partials read as
+  //    float4 and added in cluster order
+  for (int i = threadIdx.x; i < RS; i += NT) {
+    const int d = r0 + i;
+    wo[i] = d < D ? a.w[d] : 0.f;
+    const float4* src = reinterpret_cast<const float4*>(a.ypart + (int64_t)d * a.pstride);
+    float sum = 0.f;
+#pragma unroll 8
+    for (int g4 = 0; g4 < a.pstride / 4; ++g4) {
+      const float4 v = src[g4];
+      sum += v.x;
+      sum += v.y;
+      sum += v.z;
+      sum += v.w;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float v = sum[q];
-#pragma unroll
-      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      const int i = i0 + q;
-      if (lane == 0 && i < RS) ys[i] = (r0 + i < D) ? v / a.denom : 0.f;
-    }
+    ys[i] = d < D ? sum / a.denom : 0.f;
   }
-  cluster.sync();
-  // 2. deflation u = y - sum_m P_m y (prefix-sum form; all operands in smem)
+  __syncthreads();
+  // 2. deflation
   if (a.defl.nprev > 0) {
+    cluster.sync();
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * kFinThreads;
-      if (i < a.D_pad) yfull[i] = cluster.map_shared_rank(ys, i / RS)[i % RS];
-      if (i < a.D_pad) cbuf[i] = 0.f;
+      const int i = threadIdx.x + k * NT;
+      if (i < a.D_pad) {
+        yfull[i] = cluster.map_shared_rank(ys, i / RS)[i % RS];
+        cbuf[i] = 0.f;
+      }
     }
     __syncthreads();
     for (int m = m0; m < a.defl.nprev; m += CS) {
-      if (m != m0) {  // more components than CTAs: load this one (rare)
-        const float* wm = a.defl.P + (int64_t)m * a.defl.ldp;
-        for (int i = threadIdx.x; i < D; i += kFinThreads) {
+      const float* wm = a.defl.P + (int64_t)m * a.defl.ldp;
+      if (m != m0) {  // more components than CTAs
+        for (int i = threadIdx.x; i < D; i += NT) {
           wm_s[i] = wm[i];
           if (a.defl.op != MAPI_OP_DOT) {
             cs_s[i] = a.defl.csort[(int64_t)m * a.defl.stride + i];
@@ -699,18 +542,18 @@ __global__ void __launch_bounds__(kFinThreads) k_pair_finish(FinishArgs a) {
       }
       if (a.defl.op == MAPI_OP_DOT) {
         Kahan kd;
-        for (int i = threadIdx.x; i < D; i += kFinThreads) kd.add(wm_s[i] * yfull[i]);
-        const float dv = block_sum<kFinThreads>(kd.value(), red);
+        for (int i = threadIdx.x; i < D; i += NT) kd.add(wm_s[i] * yfull[i]);
+        const float dv = block_sum<NT>(kd.value(), red);
         if (threadIdx.x == 0) dotv = dv;
         __syncthreads();
-        for (int i = threadIdx.x; i < D; i += kFinThreads) cbuf[i] += wm_s[i] * dotv;
+        for (int i = threadIdx.x; i < D; i += NT) cbuf[i] += wm_s[i] * dotv;
         __syncthreads();
         continue;
       }
       const bool two = a.defl.op == MAPI_OP_MIN2;
 #pragma unroll
       for (int k = 0; k < PER; ++k) {
-        const int p = threadIdx.x + k * kFinThreads;
+        const int p = threadIdx.x + k * NT;
         float z = 0.f, y = 0.f, c = 0.f;
         if (p < D) {
           const int i = perm_s[p];
@@ -726,14 +569,14 @@ __global__ void __launch_bounds__(kFinThreads) k_pair_finish(FinishArgs a) {
         }
       }
       __syncthreads();
-      block_scan4<kFinThreads>(sA, wtot);
-      block_scan4<kFinThreads>(sB, wtot);
+      block_scan4<NT>(sA, wtot);
+      block_scan4<NT>(sB, wtot);
       if (two) {
-        block_scan4<kFinThreads>(sA2, wtot);
-        block_scan4<kFinThreads>(sB2, wtot);
+        block_scan4<NT>(sA2, wtot);
+        block_scan4<NT>(sB2, wtot);
       }
       const float totB = sB[D - 1], totB2 = two ? sB2[D - 1] : 0.f;
-      for (int i = threadIdx.x; i < D; i += kFinThreads) {
+      for (int i = threadIdx.x; i < D; i += NT) {
         const float wi = wm_s[i], ci = fabsf(wi);
         const int q = ub_s[i];
         float v = sgnf(wi) * (sA[q] + ci * (totB - sB[q]));
@@ -743,52 +586,45 @@ __global__ void __launch_bounds__(kFinThreads) k_pair_finish(FinishArgs a) {
       __syncthreads();
     }
     cluster.sync();
-    // own rows minus every CTA's products: lane q reads CTA q's value, a
-    // fixed butterfly adds them; four rows in flight per warp
     const int nq = min(CS, a.defl.nprev);
-    for (int i0 = warp * 4; i0 < RS; i0 += NW * 4) {
-      float v[4];
+    for (int i = threadIdx.x; i < RS; i += NT) {
+      const int d = r0 + i;
+      float v[CS];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int i = i0 + e;
-        v[e] = (lane < nq && i < RS) ? cluster.map_shared_rank(cbuf, lane)[r0 + i] : 0.f;
-      }
+      for (int q = 0; q < CS; ++q) v[q] = q < nq ? cluster.map_shared_rank(cbuf, q)[d] : 0.f;
+      float sub = 0.f;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-#pragma unroll
-        for (int o = 16; o; o >>= 1) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
-        const int i = i0 + e;
-        if (lane == 0 && i < RS) u[i] = (r0 + i < D) ? ys[i] - v[e] : 0.f;
-      }
+      for (int q = 0; q < CS; ++q) sub += v[q];
+      u[i] = d < D ? ys[i] - sub : 0.f;
     }
-    __syncthreads();
   } else {
-    for (int i = threadIdx.x; i < RS; i += kFinThreads) u[i] = ys[i];
-    __syncthreads();
+    for (int i = threadIdx.x; i < RS; i += NT) u[i] = ys[i];
   }
-  // 3. norm partial of own rows
+  __syncthreads();
+  // 3. norm over the cluster
   Kahan k;
-  for (int i = threadIdx.x; i < RS; i += kFinThreads) {
+  for (int i = threadIdx.x; i < RS; i += NT) {
     const float x = u[i];
     k.add(a.norm_l2 ? x * x : fabsf(x));
   }
-  const float np = block_sum<kFinThreads>(k.value(), red);
+  const float np = block_sum<NT>(k.value(), red);
   if (threadIdx.x == 0) part[0] = np;
   cluster.sync();
   float L = cluster_sum(cluster, &part[0], CS, &part[2]);
   if (a.norm_l2) L = sqrtf(L);
   const bool ok = (L > 0.f) && isfinite(L);
+  // 4. normalise own rows, delta
   Kahan dk;
   if (ok) {
-    for (int i = threadIdx.x; i < RS; i += kFinThreads) {
+    for (int i = threadIdx.x; i < RS; i += NT) {
       const int d = r0 + i;
       if (d >= D) continue;
-      const float x = u[i] / L;
+      const float x = u[i] / L;  // the n divisions of §2.2
       dk.add(fabsf(x - wo[i]));
       a.w_next[d] = x;
     }
   }
-  const float dp = block_sum<kFinThreads>(dk.value(), red);
+  const float dp = block_sum<NT>(dk.value(), red);
   if (threadIdx.x == 0) part[1] = dp;
   cluster.sync();
   const float Dsum = (r == 0) ? cluster_sum(cluster, &part[1], CS, &part[3]) : 0.f;
@@ -804,8 +640,196 @@ __global__ void __launch_bounds__(kFinThreads) k_pair_finish(FinishArgs a) {
       if (a.ctl->tol > 0.f && Dsum < a.ctl->tol) st->done = 1;
     }
     a.ctl->all_done = st->done;
+    a.ctl->counter = 0;
+    __threadfence();
+  }
+  cluster.sync();  // peers may still read this CTA's shared memory until here
+}
+
+template <int OP, int ST, int RW>
+__global__ void __launch_bounds__(kPairWarps * 32, 2)
+    k_pair_partial(const __grid_constant__ CUtensorMap xmap, PairArgs a) {
+  using PC = PairCols<ST>;
+  constexpr int CPL = PC::CPL;
+  constexpr int TC = 32 * CPL;   // columns per tile
+  constexpr int RC = kPairWarps * RW;
+  constexpr unsigned kStageBytes = RC * 128;
+  cg::cluster_group cluster = cg::this_cluster();
+  const unsigned crank = cluster.block_rank();
+  const int cid = blockIdx.x / kPairCluster;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rbase = (int)crank * RC + warp * RW;  // first row of this warp
+
+  extern __shared__ __align__(1024) uint32_t stage[];   // kPairStages x RC x 32 words
+  __shared__ __align__(8) uint64_t full[kPairStages];   // TMA tile arrived
+  // exchange slots of the column partials, by tile index mod 4: with phase B
+  // one tile behind phase A, a peer can be at most three tiles ahead of this
+  // CTA's reads (its push of tile j + 4 waits, through its phase B of tile
+  // j + 2, for this CTA's push of tile j + 2, which follows this CTA's phase
+  // B of tile j)
+  __shared__ __align__(8) uint64_t tready[4];           // all 4 column partials arrived
+  __shared__ float4 wp[RC];                 // (lo, hi, s, 0) per row of this CTA
+  __shared__ float tbuf[2][kPairWarps][TC];  // per-warp column partials (by tile parity)
+  __shared__ float tin[4][kPairCluster][TC];  // column partials pushed by each CTA
+  __shared__ int s_err;
+  __shared__ int s_last;
+
+  const int nmine = a.ntiles > cid ? (a.ntiles - cid + a.nclusters - 1) / a.nclusters : 0;
+  if (threadIdx.x == 0) {
+    s_err = 0;
+    s_last = 0;
+    for (int s = 0; s < kPairStages; ++s) mbar_init(&full[s], 1);
+    for (int q = 0; q < 4; ++q) mbar_init(&tready[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int j) {
+    const int s = j % kPairStages;
+    const int tile = cid + j * a.nclusters;
+    mbar_expect_tx(&full[s], kStageBytes);
+    tma_load_2d(stage + (size_t)s * RC * 32, &xmap, tile * TC, (int)crank * RC, &full[s]);
+  };
+  // X does not depend on the previous step: start streaming it before waiting
+  // for that step (programmatic dependent launch)
+  const int npre = nmine < kPairStages ? nmine : kPairStages;
+  if (threadIdx.x == 0)
+    for (int j = 0; j < npre; ++j) issue(j);
+  cudaGridDependencySynchronize();
+  if (*(volatile const int*)&a.ctl->all_done) {
+    // nothing left to do: let the copies already issued land, then leave
+    if (threadIdx.x == 0)
+      for (int j = 0; j < npre; ++j) mbar_wait(&full[j], 0);
+    __syncthreads();
+    return;
+  }
+  for (int r = threadIdx.x; r < RC; r += blockDim.x) {
+    const int d = (int)crank * RC + r;
+    const float wv = d < a.D ? a.w[d] : 0.f;
+    const auto p = Op<OP>::prep(wv);
+    if constexpr (OP == MAPI_OP_DOT) wp[r] = make_float4(p.w, 0.f, 0.f, 0.f);
+    else wp[r] = make_float4(p.lo, p.hi, p.s, 0.f);
+  }
+  __syncthreads();
+  // peers push into tin / tready only after the cluster has started
+  cluster.sync();
+
+  float acc[RW];
+#pragma unroll
+  for (int j = 0; j < RW; ++j) acc[j] = 0.f;
+
+  // Phase A of tile j: read this warp's rows of the stage into registers,
+  // column partials -> tbuf[j & 1] -> (after the CTA barrier) warp 0 pushes
+  // the CTA's partials to every CTA of the cluster.  The stage is refilled
+  // as soon as every warp has read it.
+  auto phase_a = [&](int j, uint32_t (&raw)[RW]) {
+    const int s = j % kPairStages;
+    const int par = j & 1;   // tbuf slot
+    const int slot = j & 3;  // exchange slot
+    if (!mbar_wait(&full[s], (unsigned)((j / kPairStages) & 1))) s_err = 1;
+    const uint32_t* src = stage + (size_t)s * RC * 32 + (size_t)(warp * RW) * 32 + lane;
+#pragma unroll
+    for (int jj = 0; jj < RW; ++jj) raw[jj] = src[jj * 32];
+    float tp[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) tp[c] = 0.f;
+#pragma unroll
+    for (int jj = 0; jj < RW; ++jj) {
+      float x[CPL];
+      PC::get(raw[jj], x);
+      const float4 q = wp[warp * RW + jj];
+      typename Op<OP>::P p;
+      if constexpr (OP == MAPI_OP_DOT) p = {q.x};
+      else p = {q.x, q.y, q.z};
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) tp[c] = Op<OP>::term(x[c], p, tp[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) tbuf[par][warp][lane * CPL + c] = tp[c];
+    __syncthreads();
+    if (threadIdx.x == 0 && j + kPairStages < nmine && !s_err) issue(j + kPairStages);
+    if (warp == 0) {
+      if (lane == 0) mbar_expect_tx(&tready[slot], kPairCluster * TC * 4);
+      __syncwarp();
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < kPairWarps; ++w) sum += tbuf[par][w][lane * CPL + c];
+        const uint32_t loc = smem_u32(&tin[slot][crank][lane * CPL + c]);
+        const uint32_t bar = smem_u32(&tready[slot]);
+#pragma unroll
+        for (int q = 0; q < kPairCluster; ++q)
+          st_async_f32(mapa_u32(loc, q), sum, mapa_u32(bar, q));
+      }
+    }
+  };
+  // Phase B of tile j: wait for the cluster's partials of its columns (they
+  // were pushed while phase A of the next tile ran), then the row sums.
+  auto phase_b = [&](int j, const uint32_t (&raw)[RW]) {
+    const int slot = j & 3;
+    if (!mbar_wait(&tready[slot], (unsigned)((j >> 2) & 1))) s_err = 1;
+    typename Op<OP>::P tpar[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      float t = 0.f;
+#pragma unroll
+      for (int r = 0; r < kPairCluster; ++r) t += tin[slot][r][lane * CPL + c];
+      tpar[c] = Op<OP>::prep(t);
+    }
+#pragma unroll
+    for (int jj = 0; jj < RW; ++jj) {
+      float x[CPL];
+      PC::get(raw[jj], x);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) acc[jj] = Op<OP>::term(x[c], tpar[c], acc[jj]);
+    }
+  };
+  // two tiles in flight: A(j) overlaps the cluster exchange of tile j - 1
+  uint32_t rawA[RW], rawB[RW];
+  int j = 0;
+#pragma unroll 1
+  for (; j + 1 < nmine; j += 2) {
+    phase_a(j, rawA);
+    if (j > 0) phase_b(j - 1, rawB);
+    phase_a(j + 1, rawB);
+    phase_b(j, rawA);
+  }
+  if (j < nmine) {
+    phase_a(j, rawA);
+    if (j > 0) phase_b(j - 1, rawB);
+    phase_b(j, rawA);
+  } else if (nmine > 0) {
+    phase_b(nmine - 1, rawB);
+  }
+  // row sums across the 32 lanes, written once per cluster
+#pragma unroll
+  for (int jj = 0; jj < RW; ++jj) {
+    float sum = acc[jj];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) a.ypart[(int64_t)(rbase + jj) * a.pstride + cid] = sum;
+  }
+  if (threadIdx.x == 0 && s_err) {
+    // a tile or a peer's partials never arrived: report it; the solve stops
+    a.ctl->v[0].status = MAPI_ETIMEOUT;
+    a.ctl->v[0].done = 1;
+  }
+  // the next step's kernel may launch now (it waits for this grid to finish
+  // before it reads anything this step writes)
+  cudaTriggerProgrammaticLaunchCompletion();
+  // last-cluster election: the cluster that finishes last runs the epilogue
+  __syncthreads();
+  if (threadIdx.x == 0) __threadfence();
+  cluster.sync();
+  if (crank == 0 && threadIdx.x == 0) {
+    const unsigned t = atomicAdd(&a.ctl->counter, 1u);
+    const int last = (t == (unsigned)a.nclusters - 1) ? 1 : 0;
+    for (int q = 0; q < kPairCluster; ++q) *cluster.map_shared_rank(&s_last, q) = last;
   }
   cluster.sync();
+  if (!s_last) return;
+  __threadfence();
+  pair_epilogue<RC>(a, cluster, reinterpret_cast<float*>(stage));
 }
 
 // Copy a finished component's step count and status out of the control
@@ -934,7 +958,10 @@ static mapi_status plan_pair(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, PairL
     return fail(ctx, MAPI_EINVAL, "pair mode supports F32 and BF16 storage");
   }
   const int rc = kPairWarps * rw;
-  pl->smem = (size_t)kPairStages * rc * 128;
+  const int d_pad = kPairCluster * rc;
+  // the stage ring, reused by the last cluster's epilogue
+  pl->smem = std::max((size_t)kPairStages * rc * 128,
+                      (size_t)pair_epi_floats(rc, d_pad) * sizeof(float));
   MAPI_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)pl->smem));
   // the tensor map: X as [rows_pad][ld] with a (tc x rc) box; rows and
@@ -970,101 +997,47 @@ static mapi_status plan_pair(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, PairL
   return MAPI_OK;
 }
 
-// ys, u, wo (own rows), yfull, cbuf (D_pad each), four scan buffers and the
-// component's w, sorted c, perm and ub (kDeflMaxD each)
-static size_t finish_smem(int D_pad, int cs) {
-  return (size_t)(3 * (D_pad / cs) + 2 * D_pad + 8 * kDeflMaxD) * sizeof(float);
-}
-
-static int finish_cluster_size(mapi_ctx* ctx, int D_pad) {
-  static int cached = 0;
-  if (cached) return cached;
-  cudaFuncSetAttribute(k_pair_finish, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  for (int cs : {16, 8, 4}) {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(cs, 1, 1);
-    cfg.blockDim = dim3(kFinThreads, 1, 1);
-    cfg.dynamicSmemBytes = finish_smem(D_pad, cs);
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_pair_finish, &cfg) == cudaSuccess && n > 0) {
-      cached = cs;
-      return cs;
-    }
-    cudaGetLastError();
-  }
-  (void)ctx;
-  return 0;
-}
+static int pair_pstride(int nclusters) { return (nclusters + 3) / 4 * 4; }
 
 static mapi_status launch_pair_step(mapi_ctx* ctx, cudaStream_t s, const PairLaunch& pl,
                                     const mapi_mat* X, const float* w, float* w_next,
-                                    float* ypart, const DeflArgs& defl, int fcs,
-                                    IterCtl* ctl, int norm_l2, float denom) {
+                                    float* ypart, const DeflArgs& defl, IterCtl* ctl,
+                                    int norm_l2, float denom) {
   PairArgs pa;
   pa.D = X->rows;
   const int TC = (X->storage == MAPI_ST_F32) ? 32 : 64;
   pa.ntiles = (int)((X->ld + TC - 1) / TC);
   pa.nclusters = pl.clusters;
   pa.w = w;
+  pa.w_next = w_next;
   pa.ypart = ypart;
+  pa.pstride = pair_pstride(pl.clusters);
   pa.D_pad = kPairCluster * kPairWarps * pl.rw;
   pa.ctl = ctl;
-  {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kPairCluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(kPairCluster * pl.clusters, 1, 1);
-    cfg.blockDim = dim3(kPairWarps * 32, 1, 1);
-    cfg.dynamicSmemBytes = pl.smem;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    void* args[] = {(void*)&pl.map, &pa};
-    cudaEvent_t ev = prof_begin(ctx, s);
-    MAPI_CUDA_TRY(ctx, cudaLaunchKernelExC(&cfg, pl.fn, args));
-    prof_end(ctx, s, ev, MAPI_KC_PAIR, (double)X->rows * X->cols * elem_bytes(X->storage),
-             2.0 * X->rows * X->cols);
-    count_launch(ctx);
-  }
-  FinishArgs fa;
-  fa.ypart = ypart;
-  fa.nparts = pl.clusters;
-  fa.D = X->rows;
-  fa.D_pad = pa.D_pad;
-  fa.defl = defl;
-  fa.w = w;
-  fa.w_next = w_next;
-  fa.ctl = ctl;
-  fa.norm_l2 = norm_l2;
-  fa.denom = denom;
-  {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = fcs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(fcs, 1, 1);
-    cfg.blockDim = dim3(kFinThreads, 1, 1);
-    cfg.dynamicSmemBytes = finish_smem(pa.D_pad, fcs);
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaEvent_t ev = prof_begin(ctx, s);
-    MAPI_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, k_pair_finish, fa));
-    prof_end(ctx, s, ev, MAPI_KC_PAIR_FINISH, 4.0 * pl.clusters * pa.D_pad, 0.0);
-    count_launch(ctx);
-  }
+  pa.defl = defl;
+  pa.norm_l2 = norm_l2;
+  pa.denom = denom;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kPairCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  // the step may start streaming X while the previous one finishes
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = dim3(kPairCluster * pl.clusters, 1, 1);
+  cfg.blockDim = dim3(kPairWarps * 32, 1, 1);
+  cfg.dynamicSmemBytes = pl.smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  void* args[] = {(void*)&pl.map, &pa};
+  cudaEvent_t ev = prof_begin(ctx, s);
+  MAPI_CUDA_TRY(ctx, cudaLaunchKernelExC(&cfg, pl.fn, args));
+  prof_end(ctx, s, ev, MAPI_KC_PAIR, (double)X->rows * X->cols * elem_bytes(X->storage),
+           2.0 * X->rows * X->cols);
+  count_launch(ctx);
   return MAPI_OK;
 }
 
@@ -1093,7 +1066,7 @@ struct PcaPlan {
   float* Q = nullptr;
   // pair mode
   PairLaunch pl;
-  int D_pad = 0, fcs = 0;
+  int D_pad = 0;
   int64_t wst = 0;
   void* defl = nullptr;
 };
@@ -1130,7 +1103,10 @@ mapi_status pca_enqueue(mapi_ctx* ctx, cudaStream_t s, const mapi_mat* X, const 
     }
     return MAPI_OK;
   }
-  // pair mode
+  // pair mode; the padding columns of the partial rows must read as zero
+  MAPI_CUDA_TRY(ctx, cudaMemsetAsync(ctx->ypart.p, 0,
+                                     sizeof(float) * (size_t)pair_pstride(p.pl.clusters) * p.D_pad,
+                                     s));
   float* wb0 = (float*)ctx->wbuf0.p;
   float* wb1 = (float*)ctx->wbuf1.p;
   IterCtl* ctl = (IterCtl*)ctx->ctl.p;
@@ -1161,7 +1137,7 @@ mapi_status pca_enqueue(mapi_ctx* ctx, cudaStream_t s, const mapi_mat* X, const 
     for (int t = 0; t < p.iters; ++t) {
       const float* wc = (t & 1) ? wb1 : wb0;
       float* wn = (t & 1) ? wb0 : wb1;
-      if ((st = launch_pair_step(ctx, s, p.pl, X, wc, wn, (float*)ctx->ypart.p, defl, p.fcs, ctl,
+      if ((st = launch_pair_step(ctx, s, p.pl, X, wc, wn, (float*)ctx->ypart.p, defl, ctl,
                                  norm_l2, (float)p.denom)) != MAPI_OK)
         return st;
     }
@@ -1210,13 +1186,11 @@ mapi_status run_pca(mapi_ctx* ctx, const mapi_mat* X, int k, int mode, mapi_op o
   } else {
     if ((st = plan_pair(ctx, X, op, &p.pl)) != MAPI_OK) return st;
     p.D_pad = kPairCluster * kPairWarps * p.pl.rw;
-    p.fcs = finish_cluster_size(ctx, p.D_pad);
-    if (!p.fcs) return fail(ctx, MAPI_ECUDA, "finish kernel: no cluster fits");
-    if ((p.D_pad / p.fcs) % 8 != 0) return fail(ctx, MAPI_EINVAL, "unsupported pair-mode row count");
     p.wst = (p.D_pad + 15) / 16 * 16;
     if ((st = ensure(ctx, ctx->wbuf0, sizeof(float) * p.wst)) != MAPI_OK ||
         (st = ensure(ctx, ctx->wbuf1, sizeof(float) * p.wst)) != MAPI_OK ||
-        (st = ensure(ctx, ctx->ypart, sizeof(float) * (size_t)p.pl.clusters * p.D_pad)) != MAPI_OK ||
+        (st = ensure(ctx, ctx->ypart,
+                     sizeof(float) * (size_t)pair_pstride(p.pl.clusters) * p.D_pad)) != MAPI_OK ||
         (st = ensure(ctx, ctx->ctl, sizeof(IterCtl))) != MAPI_OK ||
         (st = ensure(ctx, ctx->pca_defl, sizeof(int) * 3 * (size_t)k * p.D_pad)) != MAPI_OK)
       return st;

@@ -79,6 +79,24 @@ def test_pair_mode_ragged_shapes(mapi_ctx, D):
         M.mapi_matrix_free(mapi_ctx, mat)
 
 
+@pytest.mark.parametrize("st", ["f32", "bf16"])
+def test_pair_mode_many_tiles_per_cluster(mapi_ctx, st):
+    """N = 32768: every cluster streams a dozen or more column tiles, so the
+    tile pipeline and the cluster exchange slots wrap around many times."""
+    D, N, k, T = 256, 32768, 2, 6
+    X = spiked(D, N, seed=41)
+    W0 = np.stack([datagen.start_vector(D, seed=410 + c) for c in range(k)])
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(X), st)
+    try:
+        P, _ = M.mapi_pca_topk(mapi_ctx, mat, k, "pair", "min1", T, float(N), to_dev(W0))
+        Xs = X.astype(np.float64) if st == "f32" else oracle.quant_bf16(X)
+        _, Po, _ = oracle.pca_topk("pair", "min1", Xs, k, T, float(N), W0.T)
+        for c in range(k):
+            assert rel_l1(to_host(P)[c], Po[:, c]) <= TOL32
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
+
+
 def test_pair_mode_bf16(mapi_ctx):
     D, N = 256, 4096
     X = spiked(D, N, seed=31)
