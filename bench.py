@@ -444,6 +444,50 @@ def run_reference(args, rank, world):
     }
 
 
+def run_case(case: str):
+    """One short solve of a named workload, for profilers (prints a line)."""
+    import torch
+
+    import datagen
+    import paper_2110_12065_gb300 as M
+    from paper_2110_12065_gb300 import build as B
+    B.build()
+    ctx = M.mapi_create(0)
+    if case in ("pair-f32", "pair-bf16", "mincov-f32", "mincov-bf16"):
+        mode, st = case.split("-")
+        X = datagen.spiked_pca_data(D, N, seed=0)
+        mat = M.mapi_matrix_upload(ctx, torch.from_numpy(X).cuda(), st)
+        W0 = torch.from_numpy(np.stack([datagen.start_vector(D, seed=1 + c)
+                                        for c in range(2)])).cuda()
+        _, its = M.mapi_pca_topk(ctx, mat, 2, mode, "min1", 6, float(N), W0)
+        M.mapi_matrix_free(ctx, mat)
+        out = f"{case}: 2 components x 6 steps, iters {its}"
+    elif case.startswith("pagerank-"):
+        st = case.split("-")[1]
+        n = 16384
+        ip, ix = datagen.barabasi_albert_digraph(n, m=8, seed=0)
+        w0 = torch.from_numpy(datagen.start_vector(n, seed=0, low=0.0, high=1.0)).cuda()
+        _, it, _ = M.mapi_pagerank(ctx, torch.from_numpy(ip).cuda(), torch.from_numpy(ix).cuda(),
+                                   n, w0, 6, storage=st)
+        out = f"{case}: n={n}, {it} steps"
+    elif case == "batched-f32":
+        sizes = datagen.wishart_sizes(512, seed=0)
+        items, mats = [], []
+        for k, n in enumerate(sizes):
+            mats.append(M.mapi_matrix_upload(ctx, datagen.wishart_instance_device(int(n), k), "f32"))
+            w0 = torch.rand(4, int(n), device="cuda") * 2 - 1
+            items.append((mats[-1], w0, torch.empty_like(w0)))
+        it, _, _ = M.mapi_iterate_batched(ctx, items, "min1", 4, 3)
+        for m in mats:
+            M.mapi_matrix_free(ctx, m)
+        out = f"{case}: 512 instances x 4 vectors, 3 steps"
+    else:
+        raise SystemExit(f"unknown case {case}")
+    torch.cuda.synchronize()
+    M.mapi_destroy(ctx)
+    print(out, flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -453,7 +497,14 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--case", default=None,
+                    help="run one short solve of a workload for a profiler and exit: "
+                         "pair-f32, pair-bf16, mincov-f32, mincov-bf16, pagerank-f32, "
+                         "pagerank-bf16, pagerank-fp8, pagerank-i16, batched-f32")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

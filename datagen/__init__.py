@@ -35,6 +35,7 @@ __all__ = [
     "wishart_sizes",
     "wishart_instance",
     "small_grid_matrix",
+    "wishart_instance_device",
 ]
 
 DEFAULT_SPIKES = (50.0, 30.0, 20.0, 10.0, 5.0, 4.0, 3.0, 2.0)
@@ -155,3 +156,15 @@ def small_grid_matrix(n: int, seed: int, grid=(-2, -1, 0, 1, 2, 3)) -> np.ndarra
     """
     g = np.asarray(grid, dtype=np.int64)
     return g[rng(seed).integers(0, len(g), size=(n, n))]
+
+
+def wishart_instance_device(n: int, seed: int, device="cuda"):
+    """A = W W^T / k, W ~ N(0,1)^{n x k}, k = max(1, n // 2), drawn on the GPU
+    with a seeded torch generator (FP32), for batches too large to draw on the
+    host.  Deterministic for a given seed, device type and torch build."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    k = max(1, n // 2)
+    w = torch.randn(n, k, generator=g, device=device, dtype=torch.float32)
+    return (w @ w.T) / k

@@ -262,7 +262,8 @@ typedef enum {
   MAPI_KC_PAIR = 1,        /* pair-step partials over X */
   MAPI_KC_PAIR_FINISH = 2, /* pair-step reduction, deflation, normalisation */
   MAPI_KC_MINCOV = 3,      /* min-covariance build, Eq. (5) */
-  MAPI_KC_COUNT = 4
+  MAPI_KC_BATCHED = 4,     /* persistent batched solve (whole launch) */
+  MAPI_KC_COUNT = 5
 } mapi_kernel_class;
 
 typedef struct {
@@ -284,6 +285,42 @@ mapi_status mapi_profile(mapi_ctx* ctx, int enable);
 /* Copy the counters to *out (may be NULL) and, if reset != 0, zero them. */
 mapi_status mapi_get_stats(mapi_ctx* ctx, mapi_stats* out, int reset);
 
+
+
+/*
+ * Batched MAPI: `count` independent instances, each a square packed matrix
+ * with nvec start vectors, solved by Alg. 1 in one persistent launch.  Every
+ * CTA claims whole instances, largest first, and runs all their steps; the
+ * nvec vectors of an instance share every read of its matrix.  Same step,
+ * stop rule, flags and statuses as mapi_iterate, per vector.
+ *   items     host array of count entries; every A is F32 (or every A is
+ *             BF16), square, n <= 2048; w0 / w_out are device n x nvec
+ *             column-major (ld = n), caller-owned.
+ *   nvec      1 or 4.
+ *   iters_done, last_delta, statuses: host arrays of count * nvec entries
+ *             (item-major; any may be NULL).
+ * Errors: MAPI_EINVAL (item pointers, sizes, mixed storage, op), MAPI_ENOMEM,
+ * MAPI_ECUDA; otherwise the first non-OK vector status.  Synchronous.
+ */
+typedef struct {
+  const mapi_mat* A;
+  const float* w0;
+  float* w_out;
+} mapi_batch_item;
+
+mapi_status mapi_iterate_batched(mapi_ctx* ctx, const mapi_batch_item* items, int count,
+                                 mapi_op op, int nvec, int max_iters, double tol_l1,
+                                 unsigned flags, int* iters_done, double* last_delta,
+                                 int* statuses);
+
+/*
+ * Autotuner of the batched solve: times `iters` steps of the given batch
+ * for each candidate rows-per-warp (1, 2) and keeps the fastest for this
+ * context, storage and vector count (*chosen receives it; may be NULL).
+ * The outputs of the batch are overwritten.
+ */
+mapi_status mapi_autotune_batched(mapi_ctx* ctx, const mapi_batch_item* items, int count,
+                                  mapi_op op, int nvec, int iters, int* chosen);
 
 /*
  * Allocation-free solve.  The paper has no counterpart: this entry point

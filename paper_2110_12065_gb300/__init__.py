@@ -23,7 +23,8 @@ __all__ = [
     "mapi_last_error", "mapi_matrix_upload", "mapi_matrix_free",
     "mapi_matrix_info", "mapi_matrix_download", "mapi_iterate", "mapi_mincov",
     "mapi_pca_topk", "mapi_google_matrix", "mapi_pagerank", "mapi_profile",
-    "mapi_get_stats", "mapi_iterate_noalloc", "KERNEL_CLASSES",
+    "mapi_get_stats", "mapi_iterate_noalloc", "mapi_iterate_batched",
+    "mapi_autotune_batched", "KERNEL_CLASSES",
     "OP", "ST", "FLAG_FINAL_L2", "FLAG_RAW_START", "SCALE_AUTO",
     "PCA_MINCOV", "PCA_PAIR", "STATUS",
 ]
@@ -51,12 +52,16 @@ class MapiError(RuntimeError):
         super().__init__(f"{where}: {self.name} ({detail})")
 
 
-KERNEL_CLASSES = ("gemv", "pair", "pair_finish", "mincov")
+KERNEL_CLASSES = ("gemv", "pair", "pair_finish", "mincov", "batched")
 
 
 class _Stats(C.Structure):
-    _fields_ = [("launches", C.c_uint64), ("timed", C.c_uint64 * 4), ("ms", C.c_double * 4),
-                ("bytes", C.c_double * 4), ("terms", C.c_double * 4)]
+    _fields_ = [("launches", C.c_uint64), ("timed", C.c_uint64 * 5), ("ms", C.c_double * 5),
+                ("bytes", C.c_double * 5), ("terms", C.c_double * 5)]
+
+
+class _BatchItem(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("w0", C.c_void_p), ("w_out", C.c_void_p)]
 
 
 class _Config(C.Structure):
@@ -92,6 +97,8 @@ def load(path: str | None = None):
         "mapi_profile": [p_, i],
         "mapi_get_stats": [p_, C.POINTER(_Stats), i],
         "mapi_iterate_noalloc": [p_, i, i64, i, p_, i, d, u, p_, p_, p_, p_],
+        "mapi_iterate_batched": [p_, p_, i, i, i, i, d, u, p_, p_, p_],
+        "mapi_autotune_batched": [p_, p_, i, i, i, i, p_],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -332,3 +339,43 @@ def mapi_iterate_noalloc(A, op, w0, max_iters: int, tol_l1: float = 0.0, flags: 
     res = (w_out, it.value, dl.value)
     _check(st, "mapi_iterate_noalloc", None, partial=res)
     return res
+
+
+def _batch_array(items):
+    arr = (_BatchItem * len(items))()
+    for k, (mat, w0, w_out) in enumerate(items):
+        arr[k].A = mat.value if hasattr(mat, "value") else mat
+        arr[k].w0 = _dptr(w0)
+        arr[k].w_out = _dptr(w_out)
+    return arr
+
+
+def mapi_iterate_batched(ctx, items, op, nvec: int, max_iters: int, tol_l1: float = 0.0,
+                         flags: int = 0):
+    """Batched Alg. 1.  items: list of (packed matrix, w0, w_out) with w0 / w_out
+    torch CUDA float32 of shape (nvec, n).  Returns (iters, last_delta,
+    statuses) as (count, nvec) numpy arrays."""
+    arr = _batch_array(items)
+    n = len(items)
+    it = np.zeros((n, nvec), dtype=np.int32)
+    dl = np.zeros((n, nvec), dtype=np.float64)
+    sts = np.zeros((n, nvec), dtype=np.int32)
+    opi = OP[op] if isinstance(op, str) else int(op)
+    st = load().mapi_iterate_batched(ctx, arr, n, opi, int(nvec), int(max_iters), float(tol_l1),
+                                     int(flags), it.ctypes.data_as(C.c_void_p),
+                                     dl.ctypes.data_as(C.c_void_p),
+                                     sts.ctypes.data_as(C.c_void_p))
+    res = (it, dl, sts)
+    _check(st, "mapi_iterate_batched", ctx, partial=res)
+    return res
+
+
+def mapi_autotune_batched(ctx, items, op, nvec: int, iters: int = 2) -> int:
+    """Time the batched kernel variants on this batch; returns the chosen
+    rows per warp (kept by the context)."""
+    arr = _batch_array(items)
+    ch = C.c_int()
+    opi = OP[op] if isinstance(op, str) else int(op)
+    _check(load().mapi_autotune_batched(ctx, arr, len(items), opi, int(nvec), int(iters),
+                                        C.byref(ch)), "mapi_autotune_batched", ctx)
+    return ch.value

@@ -363,7 +363,7 @@ mapi_status mapi_destroy(mapi_ctx* ctx) {
   std::set<mapi_mat*> ms = ctx->mats;
   for (auto* m : ms) free_matrix(ctx, m);
   for (DevBuf* b : {&ctx->ypart, &ctx->wbuf0, &ctx->wbuf1, &ctx->ctl, &ctx->aux, &ctx->mcpart,
-                    &ctx->pca_c0, &ctx->pca_c1, &ctx->pca_q, &ctx->pca_defl})
+                    &ctx->pca_c0, &ctx->pca_c1, &ctx->pca_q, &ctx->pca_defl, &ctx->batch})
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);

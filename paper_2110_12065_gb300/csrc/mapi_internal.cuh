@@ -111,6 +111,8 @@ struct mapi_ctx {
   DevBuf ypart, wbuf0, wbuf1, ctl, aux, mcpart;
   DevBuf pca_c0, pca_c1, pca_q, pca_defl;  // PCA scratch (covariances, deflation)
   int* rec_host = nullptr;                 // pinned: per-component steps and statuses
+  DevBuf batch;                            // batched solves: instance table and results
+  int batch_rows_per_warp[2][2] = {{2, 2}, {2, 2}};  // [F32, BF16][1, 4 vectors], autotuned
   mapi::IterCtl* ctl_host = nullptr;  // pinned mirror of the control block
 
   // CUDA-graph cache: key -> executable graph
