@@ -36,13 +36,16 @@ def make_batch(ctx, st, nvec, seed0=0):
 def test_batched_parity(mapi_ctx, st, op, nvec):
     mats, items, hostA, W0s = make_batch(mapi_ctx, st, nvec)
     try:
-        it, dl, sts = M.mapi_iterate_batched(mapi_ctx, items, op, nvec, 10)
-        assert (it == 10).all() and (sts == 0).all()
-        for (mat, w0, w_out), A, W0 in zip(items, hostA, W0s):
+        try:
+            it, dl, sts = M.mapi_iterate_batched(mapi_ctx, items, op, nvec, 10)
+        except M.MapiError as e:  # some vector stopped on a zero norm (min2)
+            it, dl, sts = e.partial
+        for k, ((mat, w0, w_out), A, W0) in enumerate(zip(items, hostA, W0s)):
             Ad = A.astype(np.float64) if st == "f32" else oracle.quant_bf16(A)
             got = to_host(w_out)
             for v in range(nvec):
-                _, want, _, _ = oracle.mapi(op, Ad, W0[v].astype(np.float64), 10)
+                ost, want, oit, _ = oracle.mapi(op, Ad, W0[v].astype(np.float64), 10)
+                assert sts[k, v] == ost and it[k, v] == oit
                 assert rel_l1(got[v], want) <= TOL32
     finally:
         for m in mats:
@@ -52,13 +55,19 @@ def test_batched_parity(mapi_ctx, st, op, nvec):
 def test_batched_equals_single_instance_solves(mapi_ctx):
     mats, items, hostA, W0s = make_batch(mapi_ctx, "f32", 4, seed0=50)
     try:
-        it, dl, sts = M.mapi_iterate_batched(mapi_ctx, items, "min1", 4, 300, tol_l1=1e-6,
+        it, dl, sts = M.mapi_iterate_batched(mapi_ctx, items, "min1", 4, 30,
                                              flags=M.FLAG_FINAL_L2)
         for k, (mat, w0, w_out) in enumerate(items):
-            w1, it1, dl1 = M.mapi_iterate(mapi_ctx, mat, "min1", w0, 300, tol_l1=1e-6,
-                                          flags=M.FLAG_FINAL_L2)
-            assert list(it[k]) == it1
+            w1, it1, dl1 = M.mapi_iterate(mapi_ctx, mat, "min1", w0, 30, flags=M.FLAG_FINAL_L2)
+            assert list(it[k]) == it1 == [30] * 4
             assert rel_l1(to_host(w_out), to_host(w1)) <= TOL32
+        # stop rule: the two paths sum in different orders, so the step at
+        # which delta crosses the tolerance may differ by one
+        it, dl, sts = M.mapi_iterate_batched(mapi_ctx, items, "min1", 4, 300, tol_l1=1e-6)
+        for k, (mat, w0, w_out) in enumerate(items):
+            _, it1, _ = M.mapi_iterate(mapi_ctx, mat, "min1", w0, 300, tol_l1=1e-6)
+            assert np.abs(np.asarray(it[k]) - np.asarray(it1)).max() <= 1
+            assert (dl[k] < 1e-6).all() or (it[k] == 300).all()
     finally:
         for m in mats:
             M.mapi_matrix_free(mapi_ctx, m)
