@@ -2,6 +2,7 @@
 // storage decoders, streaming loads and deterministic block reductions.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -187,6 +188,117 @@ __device__ __forceinline__ uint4 ld_stream(const void* p) {
       : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
       : "l"(p));
   return r;
+}
+
+// ------------------------------------------------ async copies, mbarriers
+constexpr long long kWaitLimitNs = 2000000000LL;  // bounded waits: 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ long long globaltimer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Bounded wait on an mbarrier phase; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const uint32_t a = smem_u32(bar);
+  long long t0 = 0;
+  for (int i = 0;; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (i == 0) t0 = globaltimer_ns();
+    else if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t local, unsigned rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+// 4-byte store into a peer CTA's shared memory that completes 4 bytes of the
+// transaction count of the peer's mbarrier.
+__device__ __forceinline__ void st_async_f32(uint32_t remote_addr, float v, uint32_t remote_bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(
+                   remote_addr),
+               "r"(__float_as_uint(v)), "r"(remote_bar)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completing `bytes` of the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Stream a block of RB consecutive rows of a row-major matrix, 16-byte
+// chunks [c_beg, c_end), through an S-stage shared-memory ring of tiles of
+// RB x kRingTileBytes.  One thread issues the bulk copies; every thread calls
+// consume(tile, nchunks, first_chunk) for each tile in order, and the stage is
+// refilled once all threads have returned from it.  `full` holds S mbarriers
+// (initialised here); on a wait that times out `err` is set.
+constexpr int kRingTileBytes = 2048;
+constexpr int kRingTileChunks = kRingTileBytes / 16;
+
+template <int RB, int S, class F>
+__device__ __forceinline__ void stream_row_tiles(const uint8_t* A, int64_t row_bytes, int row0,
+                                                 int c_beg, int c_end, uint8_t* stage,
+                                                 uint64_t* full, int* err, F&& consume) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int ntiles = c_end > c_beg ? (c_end - c_beg + kRingTileChunks - 1) / kRingTileChunks : 0;
+  auto issue = [&](int t) {
+    const int s = t % S;
+    const int cb = c_beg + t * kRingTileChunks;
+    const int nch = min(kRingTileChunks, c_end - cb);
+    const uint32_t bytes = (uint32_t)nch * 16;
+    mbar_expect_tx(&full[s], RB * bytes);
+    uint8_t* dst = stage + (size_t)s * RB * kRingTileBytes;
+    const uint8_t* src = A + (int64_t)row0 * row_bytes + (int64_t)cb * 16;
+    for (int r = 0; r < RB; ++r)
+      bulk_g2s(dst + r * kRingTileBytes, src + (int64_t)r * row_bytes, bytes, &full[s]);
+  };
+  if (threadIdx.x == 0)
+    for (int t = 0; t < ntiles && t < S; ++t) issue(t);
+  for (int t = 0; t < ntiles; ++t) {
+    const int s = t % S;
+    if (!mbar_wait(&full[s], (unsigned)((t / S) & 1))) *err = 1;
+    const int cb = c_beg + t * kRingTileChunks;
+    consume(stage + (size_t)s * RB * kRingTileBytes, min(kRingTileChunks, c_end - cb), cb);
+    __syncthreads();
+    if (threadIdx.x == 0 && t + S < ntiles && !*err) issue(t + S);
+  }
 }
 
 // ------------------------------------------------------ compensated sums

@@ -67,7 +67,7 @@ def test_batched_equals_single_instance_solves(mapi_ctx):
         for k, (mat, w0, w_out) in enumerate(items):
             _, it1, _ = M.mapi_iterate(mapi_ctx, mat, "min1", w0, 300, tol_l1=1e-6)
             assert np.abs(np.asarray(it[k]) - np.asarray(it1)).max() <= 1
-            assert (dl[k] < 1e-6).all() or (it[k] == 300).all()
+            assert ((dl[k] < 1e-6) | (it[k] == 300)).all()
     finally:
         for m in mats:
             M.mapi_matrix_free(mapi_ctx, m)
