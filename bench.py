@@ -280,6 +280,13 @@ def run_gpu(args, rank, world, local_rank, dist):
     return line
 
 
+def alu_peak_terms(sm_mhz: float = 2070.0, sms: int = 152) -> float:
+    """ALU roofline of the float MAVP term: each term needs two min/max
+    instructions on the ALU pipe, which issues 64 lanes per clock per SM
+    (16 per SM sub-partition, measured), so 32 terms per clock per SM."""
+    return 32.0 * sms * sm_mhz * 1e6
+
+
 def timed(torch, fn, reps):
     fn()
     torch.cuda.synchronize()
@@ -336,6 +343,34 @@ def run_variants(M, ctx, torch, dev, X, W0d, peaks):
             "build_ms": round(mc["ms"] / max(1, mc["launches"]), 3),
             "build_terms_per_s": round(mc["terms"] / (mc["ms"] / 1e3), 1) if mc["ms"] else None,
             "iterate_us_per_step": round(gv["ms"] / max(1, gv["launches"]) * 1e3, 3)}
+
+    # batched: Wishart instances, n log-uniform in [64, 2048], 4 start vectors,
+    # one persistent launch (1024 instances x 10 steps here)
+    sizes = datagen.wishart_sizes(1024, seed=0)
+    for stg in ("f32", "bf16"):
+        mats, items = [], []
+        for k, n in enumerate(sizes):
+            mats.append(M.mapi_matrix_upload(ctx, datagen.wishart_instance_device(int(n), k), stg))
+            w0 = torch.from_numpy(np.stack([datagen.start_vector(int(n), seed=10 * k + v)
+                                            for v in range(4)])).to(dev)
+            items.append((mats[-1], w0, torch.empty_like(w0)))
+        r = M.mapi_autotune_batched(ctx, items, "min1", 4, iters=2)
+        steps = 10
+        run = lambda: M.mapi_iterate_batched(ctx, items, "min1", 4, steps)
+        ms = timed(torch, run, 2)
+        elems = float((sizes.astype(np.float64) ** 2).sum())
+        terms = elems * 4 * steps
+        eb = 4 if stg == "f32" else 2
+        peak_terms = alu_peak_terms()
+        out[f"batched_1024x4_{stg}"] = {
+            "instance_steps_per_s": round(1024 * steps / (ms / 1e3), 1),
+            "ms_per_launch": round(ms, 3), "rows_per_warp": r,
+            "terms_per_s": round(terms / (ms / 1e3), 1),
+            "alu_frac": round(terms / (ms / 1e3) / peak_terms, 4),
+            "matrix_gbs": round(elems * eb * steps / (ms / 1e3) / 1e9, 1),
+            "hbm_frac": round(elems * eb * steps / (ms / 1e3) / 1e9 / hbm, 4)}
+        for m in mats:
+            M.mapi_matrix_free(ctx, m)
 
     # plain MAPI / RPI on the n = 512 symmetric Gaussian, 200 steps
     A = datagen.symmetric_gaussian(512, seed=0).astype(np.float32)

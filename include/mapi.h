@@ -289,9 +289,12 @@ mapi_status mapi_get_stats(mapi_ctx* ctx, mapi_stats* out, int reset);
 
 /*
  * Batched MAPI: `count` independent instances, each a square packed matrix
- * with nvec start vectors, solved by Alg. 1 in one persistent launch.  Every
- * CTA claims whole instances, largest first, and runs all their steps; the
- * nvec vectors of an instance share every read of its matrix.  Same step,
+ * with nvec start vectors, solved by Alg. 1 in two persistent launches:
+ * instances with n >= 512 go to clusters of 8 CTAs (each CTA holds 1/8 of
+ * the rows and the whole iterate, norms and deltas combined over the cluster
+ * in a fixed order), the rest to single CTAs.  Clusters and CTAs claim whole
+ * instances, largest first, and run all their steps; the nvec vectors of an
+ * instance share every read of its matrix.  Same step,
  * stop rule, flags and statuses as mapi_iterate, per vector.
  *   items     host array of count entries; every A is F32 (or every A is
  *             BF16), square, n <= 2048; w0 / w_out are device n x nvec
@@ -315,7 +318,7 @@ mapi_status mapi_iterate_batched(mapi_ctx* ctx, const mapi_batch_item* items, in
 
 /*
  * Autotuner of the batched solve: times `iters` steps of the given batch
- * for each candidate rows-per-warp (1, 2) and keeps the fastest for this
+ * for each candidate rows-per-warp (1, 2, 4) and keeps the fastest for this
  * context, storage and vector count (*chosen receives it; may be NULL).
  * The outputs of the batch are overwritten.
  */

@@ -1,20 +1,28 @@
 // Batched MAPI: many independent instances, several start vectors each, in
-// one persistent launch.  Every CTA claims whole instances (largest first)
-// from an atomic counter and runs all their steps on its own; the iterates
-// and products of all vectors of an instance stay in shared memory, and each
+// one persistent launch of 8-CTA clusters.  Large instances go first, one
+// cluster each (every CTA streams 1/8 of the rows and keeps the whole
+// iterate); when they are all claimed, every CTA claims small instances on
+// its own.  Claims are largest first from atomic counters, the iterates and
+// products of all vectors of an instance stay in shared memory, and each
 // element of A read from memory serves every vector.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <numeric>
 
+#include <cooperative_groups.h>
+
 #include "device_common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace mapi {
 
 constexpr int kBatchThreads = 256;
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchMaxN = 2048;
+constexpr int kBatchCluster = 8;     // CTAs per large instance
+constexpr int kBatchLargeN = 1024;   // instances this large get a cluster
 
 // One instance as the kernel sees it.
 struct BatchDev {
@@ -30,9 +38,10 @@ struct BatchDev {
 
 struct BatchArgs {
   const BatchDev* items;
-  const int* order;   // claim order (largest first)
+  const int* order;   // claim order (largest first; the nlarge large ones lead)
   int count;
-  int* next;          // claim counter (zeroed before the launch)
+  int nlarge;
+  int* next;          // claim counters: next[0] large, next[32] small (zeroed)
   int max_iters;
   float tol;
   int raw_start;
@@ -41,35 +50,60 @@ struct BatchArgs {
 };
 
 // y = A (+) w for V vectors in shared memory; a warp owns R rows at a time,
-// its lanes stride over the row's 16-byte chunks.  w_s is [j][V], y_s [i][V].
+// its lanes stride over the row's 16-byte chunks with U = 8/R chunks per row
+// in flight (the loads of a group are issued before any of it is consumed).
+// w_s is [j][V] and zero past n up to the packed row length, so the zero
+// padding of the packed rows contributes exact zeros; y_s is [i - rb][V].
 template <int OP, int ST, int V, int R>
 __device__ __forceinline__ void cta_product(const BatchDev& it, const float* __restrict__ w_s,
-                                            float* __restrict__ y_s) {
+                                            float* __restrict__ y_s, int rb, int re) {
   using Ch = Chunk<ST>;
   constexpr int E = Ch::E;
+  constexpr int U = 8 / R;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int row0 = warp * R; row0 < it.n; row0 += kBatchWarps * R) {
+  for (int row0 = rb + warp * R; row0 < re; row0 += kBatchWarps * R) {
     float acc[R][V];
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[r][v] = 0.f;
-    for (int c = lane; c < it.chunks; c += 32) {
-      Ch ch[R];
+    const uint8_t* rowp[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int row = min(row0 + r, it.n - 1);  // rows past n repeat the last one
-        ch[r].raw = ld_stream(it.A + (int64_t)row * it.row_bytes + (int64_t)c * 16);
-      }
+    for (int r = 0; r < R; ++r)
+      rowp[r] = it.A + (int64_t)min(row0 + r, re - 1) * it.row_bytes;  // rows past re repeat
+    for (int c0 = lane; c0 < it.chunks; c0 += 32 * U) {
+      Ch ch[U][R];
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int j = c * E + e;
-        const bool live = j < it.n;  // the packed row's zero padding
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const auto p = Op<OP>::prep(live ? w_s[j * V + v] : 0.f);
+        for (int r = 0; r < R; ++r) {
+          const int c = c0 + 32 * u;
+          ch[u][r].raw = c < it.chunks ? ld_stream(rowp[r] + (int64_t)c * 16) : make_uint4(0, 0, 0, 0);
+        }
 #pragma unroll
-          for (int r = 0; r < R; ++r) acc[r][v] = Op<OP>::term(ch[r].get(e), p, acc[r][v]);
+      for (int u = 0; u < U; ++u) {
+        const int c = c0 + 32 * u;
+        if (c >= it.chunks) break;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int j = c * E + e;
+          float wv[V];
+          if constexpr (V == 4) {
+            const float4 q = *reinterpret_cast<const float4*>(w_s + j * 4);
+            wv[0] = q.x;
+            wv[1] = q.y;
+            wv[2] = q.z;
+            wv[3] = q.w;
+          } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) wv[v] = w_s[j * V + v];
+          }
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const auto p = Op<OP>::prep(wv[v]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r][v] = Op<OP>::term(ch[u][r].get(e), p, acc[r][v]);
+          }
         }
       }
     }
@@ -80,115 +114,242 @@ __device__ __forceinline__ void cta_product(const BatchDev& it, const float* __r
         float s = acc[r][v];
 #pragma unroll
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0 && row0 + r < it.n) y_s[(row0 + r) * V + v] = s;
+        if (lane == 0 && row0 + r < re) y_s[(row0 + r - rb) * V + v] = s;
       }
   }
 }
 
-template <int OP, int ST, int V, int R>
-__global__ void __launch_bounds__(kBatchThreads) k_batched(BatchArgs a) {
-  extern __shared__ float bsh[];
-  float* w_s = bsh;                       // kBatchMaxN x V
-  float* y_s = bsh + kBatchMaxN * V;      // kBatchMaxN x V
-  __shared__ float red[33];
-  __shared__ float s_norm[V], s_dl[V];
-  __shared__ int s_idx, s_done[V], s_it[V], s_st[V];
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const int k = atomicAdd(a.next, 1);
-      s_idx = k < a.count ? a.order[k] : -1;
-    }
-    __syncthreads();
-    const int idx = s_idx;
-    if (idx < 0) return;
-    const BatchDev it = a.items[idx];
-    const int n = it.n;
-    // Alg. 1 step 1 per vector
-    for (int v = 0; v < V; ++v) {
-      Kahan k;
-      int bad = 0;
-      for (int i = threadIdx.x; i < n; i += kBatchThreads) {
-        const float x = it.w0[(int64_t)v * n + i];
-        bad |= !isfinite(x);
-        k.add(x * x);
-      }
-      bad = __syncthreads_or(bad);
-      const float s = sqrtf(block_sum<kBatchThreads>(k.value(), red));
-      const bool scale = !a.raw_start && s > 0.f && !bad;
-      for (int i = threadIdx.x; i < n; i += kBatchThreads) {
-        const float x = it.w0[(int64_t)v * n + i];
-        w_s[i * V + v] = scale ? x / s : x;
-      }
-      if (threadIdx.x == 0) {
-        s_it[v] = 0;
-        s_st[v] = bad ? MAPI_ENONFINITE : (!a.raw_start && !(s > 0.f)) ? MAPI_EZERONORM : MAPI_OK;
-        s_done[v] = s_st[v] != MAPI_OK;
-        s_dl[v] = NAN;
-      }
-    }
-    __syncthreads();
-    for (int t = 0; t < a.max_iters; ++t) {
-      bool any = false;
+// Per-CTA state of the instance in flight (static shared memory).
+struct BatchShared {
+  float red[kBatchWarps * 4];
+  float part[4], dpart[4], L[4], D[4], dl[4];
+  int idx, done[4], it[4], st[4];
+};
+
+// Sums V values over the CTA; every thread gets the totals (fixed order).
+template <int V>
+__device__ __forceinline__ void block_sum_vec(float (&x)[V], float* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-      for (int v = 0; v < V; ++v) any |= !s_done[v];
-      if (!any) break;
-      cta_product<OP, ST, V, R>(it, w_s, y_s);
-      __syncthreads();
-      // Alg. 1 step 4 per vector: norm, divide, delta, stop test
+  for (int v = 0; v < V; ++v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x[v] += __shfl_xor_sync(0xffffffffu, x[v], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) red[warp * V + v] = x[v];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < kBatchWarps; ++q) t += red[q * V + v];
+    x[v] = t;
+  }
+  __syncthreads();
+}
+
+// Alg. 1 on one instance by CS CTAs of a cluster (CS = 1: this CTA alone).
+// CTA `crank` owns rows [rb, re) and keeps the whole iterate w_s ([j][V],
+// zero past n up to the packed row length); y_s holds its own rows' products.
+// A step: products of the own rows; l1 (l2 for DOT) norm partials, summed over
+// the cluster in rank order through DSMEM; then every CTA reads all ranks'
+// products, divides them by the norm (the n divisions of §2.2) into its
+// iterate, and sums the delta over its own rows, combined the same way.
+template <int OP, int ST, int V, int R, int CS>
+__device__ __forceinline__ void solve_one(const BatchArgs& a, const BatchDev& it, float* w_s,
+                                          float* y_s, int crank, BatchShared& sh) {
+  cg::cluster_group cluster = cg::this_cluster();
+  auto csync = [&]() {
+    if constexpr (CS > 1) cluster.sync();
+    else __syncthreads();
+  };
+  auto csum = [&](float* slot) {
+    float t = 0.f;
+    if constexpr (CS > 1) {
+#pragma unroll
+      for (int q = 0; q < CS; ++q) t += *cluster.map_shared_rank(slot, q);
+    } else {
+      t = *slot;
+    }
+    return t;
+  };
+  const int n = it.n;
+  const int npad = it.chunks * Chunk<ST>::E;
+  const int rpc = (n + CS - 1) / CS;
+  const int rb = min(n, crank * rpc), re = min(n, rb + rpc);
+  // Alg. 1 step 1 per vector (every CTA, the whole vector)
+  for (int v = 0; v < V; ++v) {
+    Kahan k;
+    int bad = 0;
+    for (int i = threadIdx.x; i < n; i += kBatchThreads) {
+      const float x = it.w0[(int64_t)v * n + i];
+      bad |= !isfinite(x);
+      k.add(x * x);
+    }
+    bad = __syncthreads_or(bad);
+    const float s = sqrtf(block_sum<kBatchThreads>(k.value(), sh.red));
+    const bool scale = !a.raw_start && s > 0.f && !bad;
+    for (int i = threadIdx.x; i < n; i += kBatchThreads) {
+      const float x = it.w0[(int64_t)v * n + i];
+      w_s[i * V + v] = scale ? x / s : x;
+    }
+    for (int i = n + threadIdx.x; i < npad; i += kBatchThreads) w_s[i * V + v] = 0.f;
+    if (threadIdx.x == 0) {
+      sh.it[v] = 0;
+      sh.st[v] = bad ? MAPI_ENONFINITE : (!a.raw_start && !(s > 0.f)) ? MAPI_EZERONORM : MAPI_OK;
+      sh.done[v] = sh.st[v] != MAPI_OK;
+      sh.dl[v] = NAN;
+    }
+  }
+  __syncthreads();
+  for (int t = 0; t < a.max_iters; ++t) {
+    bool any = false;
+#pragma unroll
+    for (int v = 0; v < V; ++v) any |= !sh.done[v];
+    if (!any) break;  // the same decision in every CTA of the cluster
+    cta_product<OP, ST, V, R>(it, w_s, y_s, rb, re);
+    __syncthreads();
+    float p[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) p[v] = 0.f;
+    for (int i = threadIdx.x; i < re - rb; i += kBatchThreads) {
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        if (s_done[v]) continue;  // uniform
-        Kahan k;
-        for (int i = threadIdx.x; i < n; i += kBatchThreads) {
-          const float y = y_s[i * V + v];
-          k.add(a.norm_l2 ? y * y : fabsf(y));
-        }
-        float L = block_sum<kBatchThreads>(k.value(), red);
-        if (a.norm_l2) L = sqrtf(L);
-        if (!(L > 0.f) || !isfinite(L)) {
-          if (threadIdx.x == 0) {
-            s_st[v] = (L == 0.f) ? MAPI_EZERONORM : MAPI_ENONFINITE;
-            s_done[v] = 1;
-          }
-          __syncthreads();
-          continue;
-        }
-        Kahan d;
-        for (int i = threadIdx.x; i < n; i += kBatchThreads) {
-          const float x = y_s[i * V + v] / L;
-          d.add(fabsf(x - w_s[i * V + v]));
-          w_s[i * V + v] = x;
-        }
-        const float D = block_sum<kBatchThreads>(d.value(), red);
-        if (threadIdx.x == 0) {
-          s_it[v] += 1;
-          s_dl[v] = D;
-          if (a.tol > 0.f && D < a.tol) s_done[v] = 1;
-        }
-        __syncthreads();
+        const float y = y_s[i * V + v];
+        p[v] += a.norm_l2 ? y * y : fabsf(y);
       }
     }
-    // Alg. 1 step 6 (optional) and the results
+    block_sum_vec<V>(p, sh.red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) sh.part[v] = p[v];
+    }
+    csync();  // norm partials of every rank visible
+    if (threadIdx.x < V) {
+      const float l = csum(&sh.part[threadIdx.x]);
+      sh.L[threadIdx.x] = a.norm_l2 ? sqrtf(l) : l;
+    }
+    __syncthreads();
+    float L[V], d[V];
+    bool ok[V];
+#pragma unroll
     for (int v = 0; v < V; ++v) {
-      float s = 1.f;
-      if (a.final_l2 && s_st[v] == MAPI_OK) {
-        Kahan k;
-        for (int i = threadIdx.x; i < n; i += kBatchThreads) {
-          const float x = w_s[i * V + v];
-          k.add(x * x);
+      L[v] = sh.L[v];
+      ok[v] = !sh.done[v] && L[v] > 0.f && isfinite(L[v]);
+      d[v] = 0.f;
+    }
+    for (int q = 0; q < CS; ++q) {
+      const float* src = y_s;
+      if constexpr (CS > 1) src = cluster.map_shared_rank(y_s, q);
+      const int qb = min(n, q * rpc), qe = min(n, qb + rpc);
+      const bool own = q == crank;
+      for (int i = threadIdx.x; i < qe - qb; i += kBatchThreads) {
+        float y[V], w[V];
+        if constexpr (V == 4) {
+          const float4 y4 = reinterpret_cast<const float4*>(src)[i];
+          const float4 w4 = reinterpret_cast<const float4*>(w_s)[qb + i];
+          y[0] = y4.x, y[1] = y4.y, y[2] = y4.z, y[3] = y4.w;
+          w[0] = w4.x, w[1] = w4.y, w[2] = w4.z, w[3] = w4.w;
+        } else {
+#pragma unroll
+          for (int v = 0; v < V; ++v) y[v] = src[i * V + v], w[v] = w_s[(qb + i) * V + v];
         }
-        s = sqrtf(block_sum<kBatchThreads>(k.value(), red));
-        if (!(s > 0.f)) s = 1.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const float x = ok[v] ? y[v] / L[v] : w[v];
+          if (own) d[v] += fabsf(x - w[v]);
+          w[v] = x;
+        }
+        if constexpr (V == 4) {
+          reinterpret_cast<float4*>(w_s)[qb + i] = make_float4(w[0], w[1], w[2], w[3]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < V; ++v) w_s[(qb + i) * V + v] = w[v];
+        }
       }
-      for (int i = threadIdx.x; i < n; i += kBatchThreads)
-        it.w_out[(int64_t)v * n + i] = (s == 1.f) ? w_s[i * V + v] : w_s[i * V + v] / s;
-      if (threadIdx.x == 0) {
-        it.res[2 * v] = s_it[v];
-        it.res[2 * v + 1] = s_st[v];
-        it.delta[v] = s_dl[v];
+    }
+    block_sum_vec<V>(d, sh.red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) sh.dpart[v] = d[v];
+    }
+    csync();  // every rank has read the products; delta partials visible
+    if (threadIdx.x < V) sh.D[threadIdx.x] = csum(&sh.dpart[threadIdx.x]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        if (sh.done[v]) continue;
+        if (!ok[v]) {
+          sh.st[v] = (L[v] == 0.f) ? MAPI_EZERONORM : MAPI_ENONFINITE;
+          sh.done[v] = 1;
+          continue;
+        }
+        sh.it[v] += 1;
+        sh.dl[v] = sh.D[v];
+        if (a.tol > 0.f && sh.D[v] < a.tol) sh.done[v] = 1;
       }
     }
     __syncthreads();
+  }
+  // Alg. 1 step 6 (optional) and the results (own rows)
+  for (int v = 0; v < V; ++v) {
+    float s = 1.f;
+    if (a.final_l2 && sh.st[v] == MAPI_OK) {
+      Kahan k;
+      for (int i = threadIdx.x; i < n; i += kBatchThreads) {
+        const float x = w_s[i * V + v];
+        k.add(x * x);
+      }
+      s = sqrtf(block_sum<kBatchThreads>(k.value(), sh.red));
+      if (!(s > 0.f)) s = 1.f;
+    }
+    for (int i = rb + threadIdx.x; i < re; i += kBatchThreads)
+      it.w_out[(int64_t)v * n + i] = (s == 1.f) ? w_s[i * V + v] : w_s[i * V + v] / s;
+    if (crank == 0 && threadIdx.x == 0) {
+      it.res[2 * v] = sh.it[v];
+      it.res[2 * v + 1] = sh.st[v];
+      it.delta[v] = sh.dl[v];
+    }
+  }
+  csync();  // no rank touches this instance's shared memory any more
+}
+
+// Phase 1: a cluster per large instance; phase 2: a CTA per small instance.
+template <int OP, int ST, int V, int R>
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batched(BatchArgs a) {
+  extern __shared__ float4 bsh4[];
+  float* bsh = reinterpret_cast<float*>(bsh4);
+  __shared__ BatchShared sh;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  for (;;) {
+    if (crank == 0 && threadIdx.x == 0) {
+      const int k = atomicAdd(&a.next[0], 1);
+      const int idx = k < a.nlarge ? a.order[k] : -1;
+#pragma unroll
+      for (int q = 0; q < kBatchCluster; ++q) *cluster.map_shared_rank(&sh.idx, q) = idx;
+    }
+    cluster.sync();
+    const int idx = sh.idx;
+    if (idx < 0) break;
+    // w_s: whole iterate (kBatchMaxN x V); y_s: own rows
+    solve_one<OP, ST, V, R, kBatchCluster>(a, a.items[idx], bsh, bsh + kBatchMaxN * V, crank, sh);
+  }
+  const int nsmall = a.count - a.nlarge;
+  for (;;) {
+    __syncthreads();  // sh.idx of the previous claim has been read
+    if (threadIdx.x == 0) {
+      const int k = atomicAdd(&a.next[32], 1);
+      sh.idx = k < nsmall ? a.order[a.nlarge + k] : -1;
+    }
+    __syncthreads();
+    const int idx = sh.idx;
+    if (idx < 0) return;
+    // n < kBatchLargeN: w_s and y_s of kBatchLargeN x V each
+    solve_one<OP, ST, V, R, 1>(a, a.items[idx], bsh, bsh + kBatchLargeN * V, 0, sh);
   }
 }
 
@@ -199,6 +360,7 @@ static BatchFn pick_r(int r) {
   switch (r) {
     case 1: return k_batched<OP, ST, V, 1>;
     case 2: return k_batched<OP, ST, V, 2>;
+    case 4: return k_batched<OP, ST, V, 4>;
   }
   return nullptr;
 }
@@ -236,34 +398,47 @@ namespace {
 
 struct DeviceGuardB {
   int prev = -1;
-  explicit DeviceGuardB(int dev) {
-    cudaGetDevice(&prev);
-    if (prev != dev) cudaSetDevice(dev);
+  explicit DeviceGuardB(int d) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != d) cudaSetDevice(d);
   }
   ~DeviceGuardB() {
     if (prev >= 0) cudaSetDevice(prev);
   }
 };
 
-// Launch one persistent batched solve with rows-per-warp r (items and order
-// already on the device).
 mapi_status launch_batched(mapi_ctx* ctx, mapi_op op, mapi_storage st, int V, int r,
                            const BatchArgs& args, cudaStream_t s, double args_bytes,
                            double args_terms) {
   BatchFn fn = batched_fn(op, st, V, r);
   if (!fn) return fail(ctx, MAPI_EINVAL, "batched solve: op/storage/nvec not supported");
-  const size_t smem = sizeof(float) * 2 * kBatchMaxN * V;
+  // whole iterate + a cluster rank's rows; the small phase uses 2 x kBatchLargeN
+  const size_t smem =
+      sizeof(float) * V *
+      std::max(kBatchMaxN + (kBatchMaxN + kBatchCluster - 1) / kBatchCluster, 2 * kBatchLargeN);
   MAPI_CUDA_TRY(ctx, cudaFuncSetAttribute((const void*)fn,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int occ = 0;
-  MAPI_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)fn,
-                                                                   kBatchThreads, smem));
-  if (occ < 1) return fail(ctx, MAPI_ECUDA, "batched kernel does not fit");
-  const int grid = std::min(args.count, occ * ctx->sm_count);
-  MAPI_CUDA_TRY(ctx, cudaMemsetAsync(args.next, 0, sizeof(int), s));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kBatchCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kBatchThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(kBatchCluster * ctx->sm_count, 1, 1);
+  int nclusters = 0;
+  MAPI_CUDA_TRY(ctx, cudaOccupancyMaxActiveClusters(&nclusters, (const void*)fn, &cfg));
+  if (nclusters < 1) return fail(ctx, MAPI_ECUDA, "batched kernel does not fit");
+  // enough clusters for the large instances plus a CTA per small one
+  const int want = args.nlarge + (args.count - args.nlarge + kBatchCluster - 1) / kBatchCluster;
+  nclusters = std::min(nclusters, std::max(1, want));
+  cfg.gridDim = dim3(kBatchCluster * nclusters, 1, 1);
+  MAPI_CUDA_TRY(ctx, cudaMemsetAsync(args.next, 0, 64 * sizeof(int), s));
   cudaEvent_t ev = prof_begin(ctx, s);
-  fn<<<grid, kBatchThreads, smem, s>>>(args);
-  MAPI_CUDA_TRY(ctx, cudaGetLastError());
+  MAPI_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, fn, args));
   prof_end(ctx, s, ev, MAPI_KC_BATCHED, args_bytes, args_terms);
   count_launch(ctx);
   return MAPI_OK;
@@ -326,10 +501,14 @@ extern "C" mapi_status mapi_iterate_batched(mapi_ctx* ctx, const mapi_batch_item
                                      ctx->stream));
   MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(d_order, order.data(), order_b, cudaMemcpyHostToDevice,
                                      ctx->stream));
+  // instances of n >= kBatchLargeN (a cluster each) lead `order`
+  int nlarge = 0;
+  while (nlarge < count && host[order[nlarge]].n >= kBatchLargeN) ++nlarge;
   BatchArgs a;
   a.items = d_items;
   a.order = d_order;
   a.count = count;
+  a.nlarge = nlarge;
   a.next = d_next;
   a.max_iters = max_iters;
   a.tol = (float)tol_l1;
@@ -379,7 +558,7 @@ extern "C" mapi_status mapi_autotune_batched(mapi_ctx* ctx, const mapi_batch_ite
   MAPI_CUDA_TRY(ctx, cudaEventCreate(&e1));
   float best = 1e30f;
   int best_r = 2;
-  for (int r : {1, 2}) {
+  for (int r : {1, 2, 4}) {
     *slot = r;
     mapi_status s = mapi_iterate_batched(ctx, items, count, op, nvec, 1, 0.0, MAPI_FLAG_RAW_START,
                                          nullptr, nullptr, nullptr);  // warm

@@ -13,7 +13,7 @@ from tests.helpers import rel_l1, to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-5
-SIZES = [1, 3, 64, 100, 257, 600, 1000, 2048]
+SIZES = [1, 3, 64, 100, 257, 513, 600, 1000, 2048]
 
 
 def make_batch(ctx, st, nvec, seed0=0):
@@ -79,7 +79,7 @@ def test_batched_autotune_keeps_results(mapi_ctx):
         M.mapi_iterate_batched(mapi_ctx, items, "min1", 4, 5)
         ref = [to_host(w_out).copy() for _, _, w_out in items]
         r = M.mapi_autotune_batched(mapi_ctx, items, "min1", 4, iters=2)
-        assert r in (1, 2)
+        assert r in (1, 2, 4)
         M.mapi_iterate_batched(mapi_ctx, items, "min1", 4, 5)
         for (_, _, w_out), want in zip(items, ref):
             assert rel_l1(to_host(w_out), want) <= TOL32
