@@ -297,7 +297,8 @@ mapi_status mapi_get_stats(mapi_ctx* ctx, mapi_stats* out, int reset);
  * instance share every read of its matrix.  Same step,
  * stop rule, flags and statuses as mapi_iterate, per vector.
  *   items     host array of count entries; every A is F32 (or every A is
- *             BF16), square, n <= 2048; w0 / w_out are device n x nvec
+ *             BF16), square, n <= 8192 / nvec (8192 for one vector, 2048
+ *             for four); w0 / w_out are device n x nvec
  *             column-major (ld = n), caller-owned.
  *   nvec      1 or 4.
  *   iters_done, last_delta, statuses: host arrays of count * nvec entries
@@ -324,6 +325,98 @@ mapi_status mapi_iterate_batched(mapi_ctx* ctx, const mapi_batch_item* items, in
  */
 mapi_status mapi_autotune_batched(mapi_ctx* ctx, const mapi_batch_item* items, int count,
                                   mapi_op op, int nvec, int iters, int* chosen);
+
+/* ------------------------------------------------------------------ */
+/* Serving: PCA and PageRank requests admitted as they arrive.          */
+/* ------------------------------------------------------------------ */
+
+typedef enum { MAPI_REQ_PCA = 0, MAPI_REQ_PAGERANK = 1 } mapi_req_kind;
+
+/*
+ * One served solve.  Every host pointer stays the caller's and must stay
+ * valid until mapi_poll has reported the request finished.
+ *   kind       MAPI_REQ_PCA: top-k components of X by the min-covariance
+ *              route of Alg. 2 (C = X (+) X^T / cov_denom, Eq. (5); then per
+ *              component Alg. 1 on the deflated C_c, as mapi_pca_topk with
+ *              MAPI_PCA_MINCOV).  MAPI_REQ_PAGERANK: MAPI-PageRank of §3.3 on
+ *              the Google matrix of Eq. (11), as mapi_pagerank.
+ *   op         MIN1, MIN2 or DOT.
+ *   storage    F32 or BF16: of X (PCA; C itself stays FP32) or of G.
+ *   max_iters  steps per component (PCA) or of the solve (PageRank), >= 1.
+ *   tol_l1     stop rule on ||w_{t+1} - w_t||_1 (<= 0: none).
+ *   X, D, N, k, cov_denom   PCA: X host D x N row-major FP32, columns are
+ *              samples; 1 <= k <= min(8, D); D <= 8192; cov_denom > 0.
+ *   indptr, indices, n, alpha   PageRank: host out-link CSR as
+ *              mapi_google_matrix takes it (n + 1 and indptr[n] int32
+ *              entries, 0 <= index < n), n <= 8192, alpha in [0, 1].
+ *   w0         host start vectors: D x k column-major (PCA) or n (PageRank),
+ *              each scaled to unit l2 norm first (Alg. 1 step 1).
+ *   out        host result, written before the request is reported done:
+ *              P (D x k column-major, l2-normalised components) or the
+ *              l2-normalised rank vector (n).
+ *   user       echoed in the result.
+ */
+typedef struct {
+  int kind;
+  mapi_op op;
+  mapi_storage storage;
+  int max_iters;
+  double tol_l1;
+  const float* X;
+  int D, N, k;
+  double cov_denom;
+  const int* indptr;
+  const int* indices;
+  int n;
+  double alpha;
+  const float* w0;
+  float* out;
+  void* user;
+} mapi_request;
+
+/* Outcome of a served request (filled by mapi_poll). */
+typedef struct {
+  mapi_status status;  /* OK, or why the request stopped (EZERONORM, ...,
+                          ECANCELLED, ENOMEM, ECUDA) */
+  int iters[8];        /* steps per component (PageRank: iters[0]) */
+  double last_delta;   /* last l1 change of the last component */
+  double queue_ms;     /* submit -> admission */
+  double run_ms;       /* admission -> result in `out` */
+  double latency_ms;   /* submit -> result in `out` */
+  void* user;
+} mapi_result;
+
+/*
+ * Queue a request.  A serving loop (a host thread with its own stream and
+ * device buffers, started by the first submit on ctx) admits queued requests
+ * in arrival order while the device bytes of the resident ones stay within
+ * the budget (mapi_config.hbm_budget_bytes; 0: 80 % of the device memory free
+ * when the loop starts) and at most max_slots are resident.  It builds each
+ * admitted request's matrix on the device (C, or G), keeps every iterate
+ * resident, and advances all resident solves together: each round is one
+ * persistent batched launch (as mapi_iterate_batched) of up to 25 steps per
+ * solve, after which finished components are deflated or results copied out.
+ *   ticket   receives the request's handle (> 0).
+ * Errors: MAPI_EINVAL (a field out of range, null pointer), MAPI_EBUDGET
+ * (the request alone needs more device bytes than the budget: it could never
+ * be admitted), MAPI_ECUDA, MAPI_ENOMEM.  Returns at once.
+ */
+mapi_status mapi_submit(mapi_ctx* ctx, const mapi_request* req, uint64_t* ticket);
+
+/*
+ * MAPI_EAGAIN while the request is queued or running.  Once it has finished,
+ * fills *out (may be NULL), forgets the ticket and returns the request's
+ * status.  MAPI_EINVAL for a ticket that is unknown or already reported.
+ */
+mapi_status mapi_poll(mapi_ctx* ctx, uint64_t ticket, mapi_result* out);
+
+/*
+ * Ask the loop to drop a request: a queued one finishes at once, a running
+ * one at the end of the current round; either reports MAPI_ECANCELLED
+ * (`out` is then undefined).  A request that has already finished keeps its
+ * result.  MAPI_EINVAL for an unknown ticket.
+ */
+mapi_status mapi_cancel(mapi_ctx* ctx, uint64_t ticket);
 
 /*
  * Allocation-free solve.  The paper has no counterpart: this entry point

@@ -24,7 +24,7 @@ __all__ = [
     "mapi_matrix_info", "mapi_matrix_download", "mapi_iterate", "mapi_mincov",
     "mapi_pca_topk", "mapi_google_matrix", "mapi_pagerank", "mapi_profile",
     "mapi_get_stats", "mapi_iterate_noalloc", "mapi_iterate_batched",
-    "mapi_autotune_batched", "KERNEL_CLASSES",
+    "mapi_autotune_batched", "mapi_submit", "mapi_poll", "mapi_cancel", "KERNEL_CLASSES",
     "OP", "ST", "FLAG_FINAL_L2", "FLAG_RAW_START", "SCALE_AUTO",
     "PCA_MINCOV", "PCA_PAIR", "STATUS",
 ]
@@ -38,6 +38,7 @@ FLAG_FINAL_L2 = 1
 FLAG_RAW_START = 2
 SCALE_AUTO = -(2 ** 31)
 PCA_MINCOV, PCA_PAIR = 0, 1
+REQ = {"pca": 0, "pagerank": 1}
 _CUDA_STREAM_LEGACY = 1
 
 LIB_PATH = _build_mod.LIB
@@ -62,6 +63,21 @@ class _Stats(C.Structure):
 
 class _BatchItem(C.Structure):
     _fields_ = [("A", C.c_void_p), ("w0", C.c_void_p), ("w_out", C.c_void_p)]
+
+
+class _Request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("op", C.c_int), ("storage", C.c_int),
+                ("max_iters", C.c_int), ("tol_l1", C.c_double),
+                ("X", C.c_void_p), ("D", C.c_int), ("N", C.c_int), ("k", C.c_int),
+                ("cov_denom", C.c_double), ("indptr", C.c_void_p), ("indices", C.c_void_p),
+                ("n", C.c_int), ("alpha", C.c_double), ("w0", C.c_void_p),
+                ("out", C.c_void_p), ("user", C.c_void_p)]
+
+
+class _Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int * 8), ("last_delta", C.c_double),
+                ("queue_ms", C.c_double), ("run_ms", C.c_double), ("latency_ms", C.c_double),
+                ("user", C.c_void_p)]
 
 
 class _Config(C.Structure):
@@ -99,6 +115,9 @@ def load(path: str | None = None):
         "mapi_iterate_noalloc": [p_, i, i64, i, p_, i, d, u, p_, p_, p_, p_],
         "mapi_iterate_batched": [p_, p_, i, i, i, i, d, u, p_, p_, p_],
         "mapi_autotune_batched": [p_, p_, i, i, i, i, p_],
+        "mapi_submit": [p_, C.POINTER(_Request), C.POINTER(C.c_uint64)],
+        "mapi_poll": [p_, C.c_uint64, C.POINTER(_Result)],
+        "mapi_cancel": [p_, C.c_uint64],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -379,3 +398,72 @@ def mapi_autotune_batched(ctx, items, op, nvec: int, iters: int = 2) -> int:
     _check(load().mapi_autotune_batched(ctx, arr, len(items), opi, int(nvec), int(iters),
                                         C.byref(ch)), "mapi_autotune_batched", ctx)
     return ch.value
+
+
+# host arrays of each open request (the library reads and writes them until
+# the request has finished), keyed by (context, ticket)
+_serve_keep = {}
+
+
+def _ctx_key(ctx):
+    return ctx.value if hasattr(ctx, "value") else int(ctx)
+
+
+def mapi_submit(ctx, kind, w0, op="min1", storage="bf16", max_iters: int = 100,
+                tol_l1: float = 0.0, X=None, k: int = 1, cov_denom: float | None = None,
+                indptr=None, indices=None, alpha: float = 0.85) -> int:
+    """Queue a served request (kind "pca" or "pagerank").  Host numpy inputs:
+    PCA X (D x N float32, row-major), w0 (k x D: one start vector per row);
+    PageRank indptr / indices (int32 out-link CSR), w0 (n).  Returns the
+    ticket; the result comes from mapi_poll."""
+    r = _Request()
+    r.kind = REQ[kind] if isinstance(kind, str) else int(kind)
+    r.op = OP[op] if isinstance(op, str) else int(op)
+    r.storage = ST[storage] if isinstance(storage, str) else int(storage)
+    r.max_iters = int(max_iters)
+    r.tol_l1 = float(tol_l1)
+    keep = []
+    if r.kind == REQ["pca"]:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        D, N = X.shape
+        W = np.ascontiguousarray(np.asarray(w0, dtype=np.float32).reshape(k, D))
+        out = np.zeros((k, D), dtype=np.float32)
+        r.X, r.D, r.N, r.k = X.ctypes.data, D, N, int(k)
+        r.cov_denom = float(N if cov_denom is None else cov_denom)
+        keep += [X, W]
+    else:
+        ip = np.ascontiguousarray(indptr, dtype=np.int32)
+        ix = np.ascontiguousarray(indices, dtype=np.int32)
+        n = ip.shape[0] - 1
+        W = np.ascontiguousarray(np.asarray(w0, dtype=np.float32).reshape(n))
+        out = np.zeros(n, dtype=np.float32)
+        r.indptr, r.indices, r.n, r.alpha = ip.ctypes.data, ix.ctypes.data, n, float(alpha)
+        keep += [ip, ix, W]
+    r.w0 = W.ctypes.data
+    r.out = out.ctypes.data
+    t = C.c_uint64()
+    _check(load().mapi_submit(ctx, C.byref(r), C.byref(t)), "mapi_submit", ctx)
+    _serve_keep[(_ctx_key(ctx), t.value)] = (keep, out)
+    return t.value
+
+
+def mapi_poll(ctx, ticket: int):
+    """None while the request is queued or running; afterwards a dict with
+    status (int), status_name, iters (per component), last_delta, queue_ms,
+    run_ms, latency_ms and out (the result array: k x D components, or the
+    n-vector of ranks).  Raises MapiError for an unknown ticket."""
+    res = _Result()
+    st = load().mapi_poll(ctx, C.c_uint64(int(ticket)), C.byref(res))
+    if st == 6:  # EAGAIN
+        return None
+    if st == 1:
+        _check(st, "mapi_poll", ctx)
+    keep, out = _serve_keep.pop((_ctx_key(ctx), int(ticket)), (None, None))
+    return {"status": int(res.status), "status_name": STATUS.get(int(res.status)),
+            "iters": list(res.iters), "last_delta": res.last_delta, "queue_ms": res.queue_ms,
+            "run_ms": res.run_ms, "latency_ms": res.latency_ms, "out": out}
+
+
+def mapi_cancel(ctx, ticket: int) -> None:
+    """Drop a queued or running request (it then reports ECANCELLED)."""
+    _check(load().mapi_cancel(ctx, C.c_uint64(int(ticket))), "mapi_cancel", ctx)

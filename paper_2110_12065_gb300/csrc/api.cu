@@ -355,6 +355,7 @@ mapi_status mapi_create(const mapi_config* cfg, mapi_ctx** out) {
 
 mapi_status mapi_destroy(mapi_ctx* ctx) {
   if (!ctx) return MAPI_EINVAL;
+  server_shutdown(ctx);  // served requests still open are dropped
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   for (auto& kv : ctx->graphs) destroy_graph(ctx, kv.second);

@@ -20,21 +20,11 @@ namespace mapi {
 
 constexpr int kBatchThreads = 256;
 constexpr int kBatchWarps = kBatchThreads / 32;
-constexpr int kBatchMaxN = 2048;
-constexpr int kBatchCluster = 8;     // CTAs per large instance
-constexpr int kBatchLargeN = 1024;   // instances this large get a cluster
+constexpr int kBatchIterFloats = 8192;  // iterate capacity: n_pad x V floats
+constexpr int kBatchCluster = 8;        // CTAs per large instance
+constexpr int kBatchLargeN = 1024;      // instances this large get a cluster
+constexpr int kBatchRowFloats = kBatchIterFloats / kBatchCluster;  // a rank's products
 
-// One instance as the kernel sees it.
-struct BatchDev {
-  const uint8_t* A;   // packed rows (rows_pad x ld)
-  int64_t row_bytes;
-  int n;
-  int chunks;         // 16-byte chunks per row
-  const float* w0;    // n x nvec, column-major (ld = n)
-  float* w_out;       // n x nvec, column-major (ld = n)
-  int* res;           // per vector: iters, status (2 ints)
-  float* delta;       // per vector: last delta
-};
 
 struct BatchArgs {
   const BatchDev* items;
@@ -42,10 +32,6 @@ struct BatchArgs {
   int count;
   int nlarge;
   int* next;          // claim counters: next[0] large, next[32] small (zeroed)
-  int max_iters;
-  float tol;
-  int raw_start;
-  int final_l2;
   int norm_l2;
 };
 
@@ -190,7 +176,7 @@ __device__ __forceinline__ void solve_one(const BatchArgs& a, const BatchDev& it
     }
     bad = __syncthreads_or(bad);
     const float s = sqrtf(block_sum<kBatchThreads>(k.value(), sh.red));
-    const bool scale = !a.raw_start && s > 0.f && !bad;
+    const bool scale = !it.raw_start && s > 0.f && !bad;
     for (int i = threadIdx.x; i < n; i += kBatchThreads) {
       const float x = it.w0[(int64_t)v * n + i];
       w_s[i * V + v] = scale ? x / s : x;
@@ -198,13 +184,13 @@ __device__ __forceinline__ void solve_one(const BatchArgs& a, const BatchDev& it
     for (int i = n + threadIdx.x; i < npad; i += kBatchThreads) w_s[i * V + v] = 0.f;
     if (threadIdx.x == 0) {
       sh.it[v] = 0;
-      sh.st[v] = bad ? MAPI_ENONFINITE : (!a.raw_start && !(s > 0.f)) ? MAPI_EZERONORM : MAPI_OK;
+      sh.st[v] = bad ? MAPI_ENONFINITE : (!it.raw_start && !(s > 0.f)) ? MAPI_EZERONORM : MAPI_OK;
       sh.done[v] = sh.st[v] != MAPI_OK;
       sh.dl[v] = NAN;
     }
   }
   __syncthreads();
-  for (int t = 0; t < a.max_iters; ++t) {
+  for (int t = 0; t < it.max_iters; ++t) {
     bool any = false;
 #pragma unroll
     for (int v = 0; v < V; ++v) any |= !sh.done[v];
@@ -289,15 +275,22 @@ __device__ __forceinline__ void solve_one(const BatchArgs& a, const BatchDev& it
         }
         sh.it[v] += 1;
         sh.dl[v] = sh.D[v];
-        if (a.tol > 0.f && sh.D[v] < a.tol) sh.done[v] = 1;
+        if (it.tol > 0.f && sh.D[v] < it.tol) sh.done[v] = 1;
       }
     }
     __syncthreads();
   }
-  // Alg. 1 step 6 (optional) and the results (own rows)
+  // Alg. 1 step 6 (optional, once the solve ends) and the results (own rows)
+  bool ends = it.last != 0;
+  {
+    bool all = true;
+#pragma unroll
+    for (int v = 0; v < V; ++v) all = all && sh.done[v];
+    ends = ends || all;
+  }
   for (int v = 0; v < V; ++v) {
     float s = 1.f;
-    if (a.final_l2 && sh.st[v] == MAPI_OK) {
+    if (it.final_l2 && ends && sh.st[v] == MAPI_OK) {
       Kahan k;
       for (int i = threadIdx.x; i < n; i += kBatchThreads) {
         const float x = w_s[i * V + v];
@@ -335,8 +328,9 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batched(BatchArgs a) {
     cluster.sync();
     const int idx = sh.idx;
     if (idx < 0) break;
-    // w_s: whole iterate (kBatchMaxN x V); y_s: own rows
-    solve_one<OP, ST, V, R, kBatchCluster>(a, a.items[idx], bsh, bsh + kBatchMaxN * V, crank, sh);
+    // w_s: whole iterate; y_s: own rows
+    solve_one<OP, ST, V, R, kBatchCluster>(a, a.items[idx], bsh, bsh + kBatchIterFloats, crank,
+                                           sh);
   }
   const int nsmall = a.count - a.nlarge;
   for (;;) {
@@ -411,10 +405,9 @@ mapi_status launch_batched(mapi_ctx* ctx, mapi_op op, mapi_storage st, int V, in
                            double args_terms) {
   BatchFn fn = batched_fn(op, st, V, r);
   if (!fn) return fail(ctx, MAPI_EINVAL, "batched solve: op/storage/nvec not supported");
-  // whole iterate + a cluster rank's rows; the small phase uses 2 x kBatchLargeN
-  const size_t smem =
-      sizeof(float) * V *
-      std::max(kBatchMaxN + (kBatchMaxN + kBatchCluster - 1) / kBatchCluster, 2 * kBatchLargeN);
+  // whole iterate + a cluster rank's rows; the small phase uses 2 x kBatchLargeN x V
+  static_assert(2 * kBatchLargeN * 4 <= kBatchIterFloats + kBatchRowFloats, "small phase");
+  const size_t smem = sizeof(float) * (kBatchIterFloats + kBatchRowFloats);
   MAPI_CUDA_TRY(ctx, cudaFuncSetAttribute((const void*)fn,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
@@ -446,42 +439,22 @@ mapi_status launch_batched(mapi_ctx* ctx, mapi_op op, mapi_storage st, int V, in
 
 }  // namespace
 
-extern "C" mapi_status mapi_iterate_batched(mapi_ctx* ctx, const mapi_batch_item* items,
-                                            int count, mapi_op op, int nvec, int max_iters,
-                                            double tol_l1, unsigned flags, int* iters_done,
-                                            double* last_delta, int* statuses) {
-  if (!ctx) return MAPI_EINVAL;
-  if (!items || count < 1 || (nvec != 1 && nvec != 4) || max_iters < 0)
-    return fail(ctx, MAPI_EINVAL, "bad batch arguments");
-  if (op != MAPI_OP_MIN1 && op != MAPI_OP_MIN2 && op != MAPI_OP_DOT)
-    return fail(ctx, MAPI_EINVAL, "batched solves take MIN1, MIN2 or DOT");
-  DeviceGuardB g(ctx->device);
-  mapi_storage st = MAPI_ST_F32;
-  std::vector<BatchDev> host(count);
+namespace mapi {
+
+// One launch over host-described instances (all of `st`, each with its own
+// step count, stop rule and start mode); per-vector iterations, statuses and
+// last deltas come back in res ([iters, status] per vector) and dl.
+mapi_status batched_run(mapi_ctx* ctx, cudaStream_t stream, std::vector<BatchDev>& host,
+                        mapi_op op, mapi_storage st, int V, std::vector<int>& res,
+                        std::vector<float>& dl) {
+  const int count = (int)host.size();
   std::vector<int64_t> work(count);
-  for (int i = 0; i < count; ++i) {
-    const mapi_mat* A = items[i].A;
-    if (!A || !ctx->mats.count(const_cast<mapi_mat*>(A)) || !items[i].w0 || !items[i].w_out)
-      return fail(ctx, MAPI_EINVAL, "batch item " + std::to_string(i) + ": bad pointers");
-    if (A->rows != A->cols || A->rows > kBatchMaxN)
-      return fail(ctx, MAPI_EINVAL, "batch items must be square with n <= 2048");
-    if (i == 0) st = A->storage;
-    if (A->storage != st || (st != MAPI_ST_F32 && st != MAPI_ST_BF16))
-      return fail(ctx, MAPI_EINVAL, "one F32 or BF16 storage per batch");
-    host[i].A = (const uint8_t*)A->data;
-    host[i].row_bytes = A->ld * elem_bytes(A->storage);
-    host[i].n = A->rows;
-    host[i].chunks = (int)(host[i].row_bytes / 16);
-    host[i].w0 = items[i].w0;
-    host[i].w_out = items[i].w_out;
-    work[i] = (int64_t)A->rows * A->rows;
-  }
-  const int V = pow2v(nvec);
+  for (int i = 0; i < count; ++i) work[i] = (int64_t)host[i].n * host[i].n;
   // largest instances first
   std::vector<int> order(count);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
-  // device table: items, order, counter, results
+  // device table: items, order, counters, results
   const size_t items_b = sizeof(BatchDev) * count, order_b = sizeof(int) * count;
   const size_t res_b = sizeof(int) * 2 * V * count, dl_b = sizeof(float) * V * count;
   const size_t total = items_b + order_b + 256 + res_b + dl_b + 1024;
@@ -497,10 +470,8 @@ extern "C" mapi_status mapi_iterate_batched(mapi_ctx* ctx, const mapi_batch_item
     host[i].res = d_res + 2 * V * i;
     host[i].delta = d_dl + V * i;
   }
-  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(d_items, host.data(), items_b, cudaMemcpyHostToDevice,
-                                     ctx->stream));
-  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(d_order, order.data(), order_b, cudaMemcpyHostToDevice,
-                                     ctx->stream));
+  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(d_items, host.data(), items_b, cudaMemcpyHostToDevice, stream));
+  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(d_order, order.data(), order_b, cudaMemcpyHostToDevice, stream));
   // instances of n >= kBatchLargeN (a cluster each) lead `order`
   int nlarge = 0;
   while (nlarge < count && host[order[nlarge]].n >= kBatchLargeN) ++nlarge;
@@ -510,27 +481,71 @@ extern "C" mapi_status mapi_iterate_batched(mapi_ctx* ctx, const mapi_batch_item
   a.count = count;
   a.nlarge = nlarge;
   a.next = d_next;
-  a.max_iters = max_iters;
-  a.tol = (float)tol_l1;
-  a.raw_start = (flags & MAPI_FLAG_RAW_START) ? 1 : 0;
-  a.final_l2 = (flags & MAPI_FLAG_FINAL_L2) ? 1 : 0;
   a.norm_l2 = (op == MAPI_OP_DOT) ? 1 : 0;
   const int r = ctx->batch_rows_per_warp[st == MAPI_ST_F32 ? 0 : 1][V == 1 ? 0 : 1];
-  // algorithmic work if every vector runs max_iters steps: each matrix read
+  // algorithmic work if every vector runs all its steps: each matrix read
   // once per step, n^2 terms per vector per step
   double bytes = 0.0, terms = 0.0;
   for (int i = 0; i < count; ++i) {
-    bytes += (double)work[i] * elem_bytes(st) * max_iters;
-    terms += (double)work[i] * V * max_iters;
+    bytes += (double)work[i] * elem_bytes(st) * host[i].max_iters;
+    terms += (double)work[i] * V * host[i].max_iters;
   }
-  if ((s = launch_batched(ctx, op, st, V, r > 0 ? r : 2, a, ctx->stream, bytes, terms)) != MAPI_OK)
+  if ((s = launch_batched(ctx, op, st, V, r > 0 ? r : 2, a, stream, bytes, terms)) != MAPI_OK)
     return s;
-  std::vector<int> res(2 * V * count);
-  std::vector<float> dl(V * count);
-  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(res.data(), d_res, res_b, cudaMemcpyDeviceToHost, ctx->stream));
-  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(dl.data(), d_dl, dl_b, cudaMemcpyDeviceToHost, ctx->stream));
-  MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  res.assign(2 * V * count, 0);
+  dl.assign(V * count, 0.f);
+  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(res.data(), d_res, res_b, cudaMemcpyDeviceToHost, stream));
+  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(dl.data(), d_dl, dl_b, cudaMemcpyDeviceToHost, stream));
+  MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
   prof_collect(ctx, ctx->pending, true);
+  return MAPI_OK;
+}
+
+int batched_max_n(int nvec) { return kBatchIterFloats / pow2v(nvec); }
+
+}  // namespace mapi
+
+extern "C" mapi_status mapi_iterate_batched(mapi_ctx* ctx, const mapi_batch_item* items,
+                                            int count, mapi_op op, int nvec, int max_iters,
+                                            double tol_l1, unsigned flags, int* iters_done,
+                                            double* last_delta, int* statuses) {
+  if (!ctx) return MAPI_EINVAL;
+  if (!items || count < 1 || (nvec != 1 && nvec != 4) || max_iters < 0)
+    return fail(ctx, MAPI_EINVAL, "bad batch arguments");
+  if (op != MAPI_OP_MIN1 && op != MAPI_OP_MIN2 && op != MAPI_OP_DOT)
+    return fail(ctx, MAPI_EINVAL, "batched solves take MIN1, MIN2 or DOT");
+  DeviceGuardB g(ctx->device);
+  const int V = pow2v(nvec);
+  const int nmax = batched_max_n(nvec);
+  mapi_storage st = MAPI_ST_F32;
+  std::vector<BatchDev> host(count);
+  for (int i = 0; i < count; ++i) {
+    const mapi_mat* A = items[i].A;
+    if (!A || !ctx->mats.count(const_cast<mapi_mat*>(A)) || !items[i].w0 || !items[i].w_out)
+      return fail(ctx, MAPI_EINVAL, "batch item " + std::to_string(i) + ": bad pointers");
+    if (A->rows != A->cols || A->rows > nmax)
+      return fail(ctx, MAPI_EINVAL,
+                  "batch items must be square with n <= " + std::to_string(nmax));
+    if (i == 0) st = A->storage;
+    if (A->storage != st || (st != MAPI_ST_F32 && st != MAPI_ST_BF16))
+      return fail(ctx, MAPI_EINVAL, "one F32 or BF16 storage per batch");
+    BatchDev& h = host[i];
+    h.A = (const uint8_t*)A->data;
+    h.row_bytes = A->ld * elem_bytes(A->storage);
+    h.n = A->rows;
+    h.chunks = (int)(h.row_bytes / 16);
+    h.w0 = items[i].w0;
+    h.w_out = items[i].w_out;
+    h.max_iters = max_iters;
+    h.tol = (float)tol_l1;
+    h.raw_start = (flags & MAPI_FLAG_RAW_START) ? 1 : 0;
+    h.final_l2 = (flags & MAPI_FLAG_FINAL_L2) ? 1 : 0;
+    h.last = 1;
+  }
+  std::vector<int> res;
+  std::vector<float> dl;
+  mapi_status s = batched_run(ctx, ctx->stream, host, op, st, V, res, dl);
+  if (s != MAPI_OK) return s;
   mapi_status result = MAPI_OK;
   for (int i = 0; i < count; ++i)
     for (int v = 0; v < V; ++v) {

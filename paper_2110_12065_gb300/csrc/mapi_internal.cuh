@@ -96,6 +96,10 @@ struct GraphEntry {
   std::vector<ProfMark> marks;     // event nodes inside the graph
 };
 
+namespace mapi {
+struct Server;
+}
+
 struct mapi_ctx {
   int device = 0;
   int sm_count = 0;
@@ -129,6 +133,10 @@ struct mapi_ctx {
   std::vector<ProfMark>* mark_sink = nullptr;  // where new marks go
   std::vector<cudaEvent_t> ev_pool;
   mapi_stats stats = {};
+
+  // serving loop (created by the first mapi_submit)
+  std::mutex server_mu;
+  mapi::Server* server = nullptr;
 };
 
 namespace mapi {
@@ -212,6 +220,39 @@ mapi_status launch_finish(mapi_ctx* ctx, cudaStream_t s, const float* wb0, const
 // PCA kernels (pca.cu).
 mapi_status launch_mincov_raw(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, float denom,
                               float* C, int64_t ldc, cudaStream_t s);
+size_t mincov_scratch_bytes(const mapi_ctx* ctx, const mapi_mat* X);
+// C_c = C - Q C with Q = sum_{m<c} P_m (+) P_m^T (columns of P, ldp apart);
+// C, Q and C_c are D x D row-major with leading dimension ld.
+mapi_status launch_deflate_mincov(mapi_ctx* ctx, mapi_op op, const float* P, int64_t ldp, int c,
+                                  int D, const float* C, int64_t ld, float* Q, float* Cc,
+                                  cudaStream_t s);
+
+// Batched solves (batched.cu): one instance as the kernel sees it.
+struct BatchDev {
+  const uint8_t* A;   // packed rows (rows_pad x ld)
+  int64_t row_bytes;
+  int n;
+  int chunks;         // 16-byte chunks per row
+  const float* w0;    // n x nvec, column-major (ld = n)
+  float* w_out;       // n x nvec, column-major (ld = n)
+  int* res;           // per vector: iters, status (2 ints)
+  float* delta;       // per vector: last delta
+  int max_iters;      // steps of this launch
+  float tol;          // stop rule (<= 0: none)
+  int raw_start;      // 1: w0 as given; 0: w0 / ||w0||_2 first
+  int final_l2;       // l2-normalise the result if the solve ends here
+  int last;           // the solve ends after max_iters steps (else it resumes
+                      // from w_out in a later launch)
+};
+// One persistent launch over the instances (all of storage st, nvec = V);
+// res gets [iters, status] per vector and dl the last deltas.  Synchronous.
+mapi_status batched_run(mapi_ctx* ctx, cudaStream_t stream, std::vector<BatchDev>& host,
+                        mapi_op op, mapi_storage st, int V, std::vector<int>& res,
+                        std::vector<float>& dl);
+int batched_max_n(int nvec);
+
+// Serving loop (serve.cu): stops the loop and releases what it holds.
+void server_shutdown(mapi_ctx* ctx);
 mapi_status run_pca(mapi_ctx* ctx, const mapi_mat* X, int k, int mode,
                     mapi_op op, int iters, double tol, double denom,
                     const float* w0, float* P_out, int* iters_done);

@@ -988,12 +988,24 @@ static mapi_status launch_pair_step(mapi_ctx* ctx, cudaStream_t s, const PairLau
 
 // Scratch of the min-covariance splits for X (the launcher grows it; callers
 // that capture graphs size it first).
-static size_t mincov_scratch_bytes(const mapi_ctx* ctx, const mapi_mat* X) {
+size_t mincov_scratch_bytes(const mapi_ctx* ctx, const mapi_mat* X) {
   const int T = (X->rows + kMcT - 1) / kMcT;
   const int nt = T * (T + 1) / 2;
   int nsplit = 1;
   while (nt * nsplit < 4 * ctx->sm_count && X->ld / (nsplit * 2) >= 4 * kMcK) nsplit *= 2;
   return sizeof(float) * (size_t)nsplit * nt * kMcT * kMcT;
+}
+
+mapi_status launch_deflate_mincov(mapi_ctx* ctx, mapi_op op, const float* P, int64_t ldp, int c,
+                                  int D, const float* C, int64_t ld, float* Q, float* Cc,
+                                  cudaStream_t s) {
+  mapi_status st = launch_build_Q(ctx, op, P, ldp, c, D, Q, ld, s);
+  if (st != MAPI_OK) return st;
+  dim3 g((D + 63) / 64, (D + 63) / 64);
+  k_deflate_gemm<<<g, 256, 0, s>>>(C, Q, D, ld, Cc);
+  MAPI_CUDA_TRY(ctx, cudaGetLastError());
+  count_launch(ctx);
+  return MAPI_OK;
 }
 
 namespace {
