@@ -400,7 +400,138 @@ def run_variants(M, ctx, torch, dev, X, W0d, peaks):
         out[f"pagerank_n16384_{stg}"] = {"iters_per_s": round(100 / (ms / 1e3), 1),
                                          "gemv_gbs": round(gbs, 1),
                                          "hbm_frac": round(gbs / hbm, 4)}
+    out["serve_mixed"] = run_serving(M, torch, dev)
     return out
+
+
+def serving_workload(count: int, seed: int = 0):
+    """Mixed served requests: 60 % PCA (min-covariance route; D in {256, 512,
+    1024}, N log-uniform in [4096, 65536], k uniform in 1..8, 100 steps per
+    component), 40 % PageRank (n log-uniform in [256, 8192], Barabasi-Albert
+    m = 8, alpha 0.85, 100 steps or delta < 1e-8).  Inputs come from a seeded
+    pool of 6 data sets and 6 graphs (drawing a fresh 1024 x 65536 data set
+    per request would take the host longer than the GPU needs to serve it)."""
+    import datagen
+    r = datagen.rng(seed)
+    pca_pool, pr_pool = [], []
+    for j in range(6):
+        D = (256, 512, 1024)[j % 3]
+        N = int(np.exp(r.uniform(np.log(4096), np.log(65536))))
+        pca_pool.append(datagen.spiked_pca_data(D, N, seed=100 + j))
+        n = int(np.exp(r.uniform(np.log(256), np.log(8192))))
+        pr_pool.append(datagen.barabasi_albert_digraph(n, m=8, seed=200 + j))
+    reqs = []
+    for i in range(count):
+        if r.random() < 0.6:
+            X = pca_pool[int(r.integers(0, 6))]
+            k = int(r.integers(1, 9))
+            W0 = np.stack([datagen.start_vector(X.shape[0], seed=10 * i + c) for c in range(k)])
+            reqs.append(("pca", X, k, W0))
+        else:
+            ip, ix = pr_pool[int(r.integers(0, 6))]
+            n = ip.shape[0] - 1
+            reqs.append(("pagerank", ip, ix, datagen.start_vector(n, seed=i, low=0.0, high=1.0)))
+    return reqs
+
+
+def run_serving(M, torch, dev, count: int = 48, seed: int = 0):
+    """Served (BF16, one batched launch per round) against plain (FP32, one
+    request at a time through mapi_pca_topk / mapi_pagerank).  Latency is
+    submit -> result in host memory, input upload included.  Saturation: all
+    requests submitted at once.  Poisson run: arrivals at half the served
+    saturation rate; the plain latencies at those arrivals come from a
+    single FIFO server with the measured plain service times."""
+    import datagen
+    reqs = serving_workload(count, seed)
+
+    def submit(ctx, q):
+        if q[0] == "pca":
+            _, X, k, W0 = q
+            return M.mapi_submit(ctx, "pca", W0, op="min1", storage="bf16", max_iters=100, X=X,
+                                 k=k, cov_denom=X.shape[1])
+        _, ip, ix, w0 = q
+        return M.mapi_submit(ctx, "pagerank", w0, op="min1", storage="bf16", max_iters=100,
+                             tol_l1=1e-8, indptr=ip, indices=ix)
+
+    def served(arrivals):
+        ctx = M.mapi_create(0, hbm_budget_bytes=40 << 30)
+        try:
+            # warm the loop (thread, child context, kernels) on the first request
+            t = submit(ctx, reqs[0])
+            while M.mapi_poll(ctx, t) is None:
+                time.sleep(0.001)
+            pending, lat, t0 = {}, [], time.perf_counter()
+            i = 0
+            while i < len(reqs) or pending:
+                now = time.perf_counter() - t0
+                while i < len(reqs) and arrivals[i] <= now:
+                    pending[submit(ctx, reqs[i])] = i
+                    i += 1
+                for t in list(pending):
+                    res = M.mapi_poll(ctx, t)
+                    if res is not None:
+                        assert res["status"] == 0, res
+                        lat.append(res["latency_ms"])
+                        del pending[t]
+                time.sleep(0.0005)
+            makespan = time.perf_counter() - t0
+        finally:
+            M.mapi_destroy(ctx)
+        return np.asarray(lat), makespan
+
+    def plain_service():
+        ctx = M.mapi_create(0)
+        svc = []
+        try:
+            for q in reqs:
+                t0 = time.perf_counter()
+                if q[0] == "pca":
+                    _, X, k, W0 = q
+                    Xm = M.mapi_matrix_upload(ctx, torch.from_numpy(X).to(dev), "f32")
+                    P, _ = M.mapi_pca_topk(ctx, Xm, k, "mincov", "min1", 100, X.shape[1],
+                                           torch.from_numpy(W0).to(dev))
+                    P.cpu()
+                    M.mapi_matrix_free(ctx, Xm)
+                else:
+                    _, ip, ix, w0 = q
+                    rk, _, _ = M.mapi_pagerank(ctx, torch.from_numpy(ip).to(dev),
+                                               torch.from_numpy(ix).to(dev), ip.shape[0] - 1,
+                                               torch.from_numpy(w0).to(dev), 100, tol_l1=1e-8)
+                    rk.cpu()
+                torch.cuda.synchronize()
+                svc.append((time.perf_counter() - t0) * 1e3)
+        finally:
+            M.mapi_destroy(ctx)
+        return np.asarray(svc)
+
+    def fifo(arrivals_s, svc_ms):
+        done, lat = 0.0, []
+        for a, s in zip(arrivals_s * 1e3, svc_ms):
+            done = max(done, a) + s
+            lat.append(done - a)
+        return np.asarray(lat)
+
+    pct = lambda x, q: round(float(np.percentile(x, q)), 3)
+    zero = np.zeros(len(reqs))
+    lat_sat, span_sat = served(zero)
+    svc = plain_service()
+    cap_served = len(reqs) / span_sat
+    lam = 0.5 * cap_served
+    arr = np.cumsum(datagen.rng(seed + 1).exponential(1.0 / lam, size=len(reqs)))
+    lat_p, span_p = served(arr)
+    lat_plain = fifo(arr, svc)
+    return {
+        "requests": len(reqs), "mix": "60% PCA mincov k<=8 x 100 steps, 40% PageRank 100 steps",
+        "served_dtype": "bf16 storage, f32 arithmetic", "plain_dtype": "f32",
+        "saturation": {"served_solves_per_s": round(cap_served, 2),
+                       "plain_solves_per_s": round(len(reqs) / (svc.sum() / 1e3), 2),
+                       "served_p50_ms": pct(lat_sat, 50), "served_p99_ms": pct(lat_sat, 99)},
+        "poisson": {"lambda_per_s": round(lam, 2),
+                    "served_p50_ms": pct(lat_p, 50), "served_p99_ms": pct(lat_p, 99),
+                    "served_solves_per_s": round(len(reqs) / span_p, 2),
+                    "plain_p50_ms": pct(lat_plain, 50), "plain_p99_ms": pct(lat_plain, 99)},
+        "plain_service_ms": {"p50": pct(svc, 50), "p99": pct(svc, 99)},
+    }
 
 
 # --------------------------------------------------------------- CPU arm
@@ -505,6 +636,9 @@ def run_case(case: str):
         _, it, _ = M.mapi_pagerank(ctx, torch.from_numpy(ip).cuda(), torch.from_numpy(ix).cuda(),
                                    n, w0, 6, storage=st)
         out = f"{case}: n={n}, {it} steps"
+    elif case == "serve":
+        import torch
+        out = json.dumps(run_serving(M, torch, "cuda"))
     elif case == "batched-f32":
         sizes = datagen.wishart_sizes(512, seed=0)
         items, mats = [], []
@@ -535,7 +669,7 @@ def main():
     ap.add_argument("--case", default=None,
                     help="run one short solve of a workload for a profiler and exit: "
                          "pair-f32, pair-bf16, mincov-f32, mincov-bf16, pagerank-f32, "
-                         "pagerank-bf16, pagerank-fp8, pagerank-i16, batched-f32")
+                         "pagerank-bf16, pagerank-fp8, pagerank-i16, batched-f32, serve")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)
