@@ -460,7 +460,7 @@ def run_serving(M, torch, dev, count: int = 48, seed: int = 0):
             t = submit(ctx, reqs[0])
             while M.mapi_poll(ctx, t) is None:
                 time.sleep(0.001)
-            pending, lat, t0 = {}, [], time.perf_counter()
+            pending, lat, build, t0 = {}, [], [], time.perf_counter()
             i = 0
             while i < len(reqs) or pending:
                 now = time.perf_counter() - t0
@@ -472,12 +472,13 @@ def run_serving(M, torch, dev, count: int = 48, seed: int = 0):
                     if res is not None:
                         assert res["status"] == 0, res
                         lat.append(res["latency_ms"])
+                        build.append(res["build_ms"])
                         del pending[t]
                 time.sleep(0.0005)
             makespan = time.perf_counter() - t0
         finally:
             M.mapi_destroy(ctx)
-        return np.asarray(lat), makespan
+        return np.asarray(lat), makespan, np.asarray(build)
 
     def plain_service():
         ctx = M.mapi_create(0)
@@ -513,12 +514,12 @@ def run_serving(M, torch, dev, count: int = 48, seed: int = 0):
 
     pct = lambda x, q: round(float(np.percentile(x, q)), 3)
     zero = np.zeros(len(reqs))
-    lat_sat, span_sat = served(zero)
+    lat_sat, span_sat, _ = served(zero)
     svc = plain_service()
     cap_served = len(reqs) / span_sat
     lam = 0.5 * cap_served
     arr = np.cumsum(datagen.rng(seed + 1).exponential(1.0 / lam, size=len(reqs)))
-    lat_p, span_p = served(arr)
+    lat_p, span_p, build_p = served(arr)
     lat_plain = fifo(arr, svc)
     return {
         "requests": len(reqs), "mix": "60% PCA mincov k<=8 x 100 steps, 40% PageRank 100 steps",
@@ -529,6 +530,7 @@ def run_serving(M, torch, dev, count: int = 48, seed: int = 0):
         "poisson": {"lambda_per_s": round(lam, 2),
                     "served_p50_ms": pct(lat_p, 50), "served_p99_ms": pct(lat_p, 99),
                     "served_solves_per_s": round(len(reqs) / span_p, 2),
+                    "served_build_p50_ms": pct(build_p, 50),
                     "plain_p50_ms": pct(lat_plain, 50), "plain_p99_ms": pct(lat_plain, 99)},
         "plain_service_ms": {"p50": pct(svc, 50), "p99": pct(svc, 99)},
     }

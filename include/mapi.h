@@ -381,6 +381,8 @@ typedef struct {
   int iters[8];        /* steps per component (PageRank: iters[0]) */
   double last_delta;   /* last l1 change of the last component */
   double queue_ms;     /* submit -> admission */
+  double build_ms;     /* admission -> matrix built on the device (upload,
+                          Eq. (5) or Eq. (11), packing) */
   double run_ms;       /* admission -> result in `out` */
   double latency_ms;   /* submit -> result in `out` */
   void* user;

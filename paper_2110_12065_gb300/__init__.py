@@ -76,7 +76,8 @@ class _Request(C.Structure):
 
 class _Result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int * 8), ("last_delta", C.c_double),
-                ("queue_ms", C.c_double), ("run_ms", C.c_double), ("latency_ms", C.c_double),
+                ("queue_ms", C.c_double), ("build_ms", C.c_double), ("run_ms", C.c_double),
+                ("latency_ms", C.c_double),
                 ("user", C.c_void_p)]
 
 
@@ -450,7 +451,7 @@ def mapi_submit(ctx, kind, w0, op="min1", storage="bf16", max_iters: int = 100,
 def mapi_poll(ctx, ticket: int):
     """None while the request is queued or running; afterwards a dict with
     status (int), status_name, iters (per component), last_delta, queue_ms,
-    run_ms, latency_ms and out (the result array: k x D components, or the
+    build_ms, run_ms, latency_ms and out (the result array: k x D components, or the
     n-vector of ranks).  Raises MapiError for an unknown ticket."""
     res = _Result()
     st = load().mapi_poll(ctx, C.c_uint64(int(ticket)), C.byref(res))
@@ -461,7 +462,8 @@ def mapi_poll(ctx, ticket: int):
     keep, out = _serve_keep.pop((_ctx_key(ctx), int(ticket)), (None, None))
     return {"status": int(res.status), "status_name": STATUS.get(int(res.status)),
             "iters": list(res.iters), "last_delta": res.last_delta, "queue_ms": res.queue_ms,
-            "run_ms": res.run_ms, "latency_ms": res.latency_ms, "out": out}
+            "build_ms": res.build_ms, "run_ms": res.run_ms, "latency_ms": res.latency_ms,
+            "out": out}
 
 
 def mapi_cancel(ctx, ticket: int) -> None:

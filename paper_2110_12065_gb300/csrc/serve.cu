@@ -14,13 +14,17 @@
 #include <map>
 #include <thread>
 
-#include "mapi_internal.cuh"
+#include "device_common.cuh"
 
 namespace mapi {
 
 using Clock = std::chrono::steady_clock;
 constexpr int kRoundSteps = 25;
 constexpr int kMaxComponents = 8;
+// Solves this large iterate on the whole GPU (the split GEMV, one launch per
+// step) instead of a share of the batched launch: one cluster per instance
+// would leave most SMs idle while only a few large requests are resident.
+constexpr int kWideN = 2048;
 
 struct ServeReq {
   uint64_t ticket = 0;
@@ -44,8 +48,10 @@ struct ServeReq {
   const uint8_t* A = nullptr;
   int64_t row_bytes = 0;
   mapi_storage st = MAPI_ST_F32;
+  mapi_mat view;        // the iterated matrix as the split GEMV reads it
   int comp = 0, it_comp = 0, cur = 0;
   bool resumed = false;
+  Clock::time_point t_built;
 };
 
 struct Server {
@@ -61,6 +67,10 @@ struct Server {
   size_t budget = 0, used = 0;
   int resident = 0;
   std::vector<ServeReq*> live;  // loop thread only
+  cudaStream_t batch_stream = nullptr;  // batched launches beside the wide solves
+  cudaEvent_t round_start = nullptr;    // orders batch_stream after the loop stream
+  IterCtl* wide_ctl = nullptr;          // pinned: control blocks of the wide solves
+  int wide_cap = 0;
 };
 
 namespace {
@@ -90,7 +100,7 @@ size_t request_bytes(const mapi_ctx* ctx, const mapi_request& r) {
     x.storage = r.storage;
     const size_t ldc = (size_t)(r.D + 3) / 4 * 4;
     return (size_t)r.D * r.N * 4 + packed_bytes(r.D, r.N, r.storage) +
-           mincov_scratch_bytes(ctx, &x) + 3 * (size_t)r.D * ldc * 4 +
+           mincov_scratch_bytes(ctx, &x) + 3 * (size_t)((r.D + 63) / 64 * 64) * ldc * 4 +
            (size_t)r.D * (2 * r.k + 2) * 4;
   }
   const size_t nnz = (size_t)r.indptr[r.n];
@@ -156,6 +166,7 @@ void finish(Server* sv, ServeReq* q, mapi_status s) {
   q->res.status = s;
   q->res.queue_ms = ms_between(q->t_submit, q->t_admit);
   q->res.run_ms = ms_between(q->t_admit, t);
+  q->res.build_ms = q->t_built > q->t_admit ? ms_between(q->t_admit, q->t_built) : 0.0;
   q->res.latency_ms = ms_between(q->t_submit, t);
   q->res.user = q->r.user;
   q->state = 2;
@@ -172,7 +183,8 @@ mapi_status build(Server* sv, ServeReq* q) {
   if (r.kind == MAPI_REQ_PCA) {
     const int D = r.D;
     q->ldc = (D + 3) / 4 * 4;
-    const size_t cb = sizeof(float) * (size_t)D * q->ldc;
+    const int rows_pad = (D + 63) / 64 * 64;
+    const size_t cb = sizeof(float) * (size_t)rows_pad * q->ldc;
     if ((s = mapi_matrix_upload(c, r.X, 0, MAPI_SRC_F32, D, r.N, r.N, r.storage, MAPI_SCALE_AUTO,
                                 &q->X)) != MAPI_OK)
       return s;
@@ -196,6 +208,11 @@ mapi_status build(Server* sv, ServeReq* q) {
     q->A = (const uint8_t*)q->C;
     q->row_bytes = q->ldc * 4;
     q->st = MAPI_ST_F32;
+    q->view.rows = q->view.cols = D;
+    q->view.rows_pad = rows_pad;
+    q->view.ld = q->ldc;
+    q->view.storage = MAPI_ST_F32;
+    q->view.data = q->C;
     return MAPI_OK;
   }
   const int n = r.n;
@@ -218,6 +235,8 @@ mapi_status build(Server* sv, ServeReq* q) {
   q->A = (const uint8_t*)q->G->data;
   q->row_bytes = q->G->ld * elem_bytes(q->G->storage);
   q->st = q->G->storage;
+  q->view = *q->G;
+  q->view.owner = nullptr;
   return MAPI_OK;
 }
 
@@ -251,25 +270,118 @@ mapi_status component_done(Server* sv, ServeReq* q, bool* all_done) {
                                         c->stream);
   if (s != MAPI_OK) return s;
   q->A = (const uint8_t*)q->Cc;
+  q->view.data = q->Cc;
   q->it_comp = 0;
   q->resumed = false;
   return MAPI_OK;
 }
 
-// One round over every resident solve.
+// w / ||w||_2 in place (Alg. 1's optional last step) for a wide solve that
+// met its stop rule inside a round that was not its last.
+__global__ void k_l2_normalize(float* w, int n) {
+  __shared__ float sh[33];
+  Kahan k;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) k.add(w[i] * w[i]);
+  const float s = sqrtf(block_sum<1024>(k.value(), sh));
+  if (!(s > 0.f)) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = w[i] / s;
+}
+
+struct StepOutcome {
+  int iters = 0, status = MAPI_OK;
+  float delta = 0.f;
+  bool converged_early = false;  // stop rule met in a round that was not the last
+};
+
+// Hands one round's outcome of a solve to its request; true if it ended.
+bool absorb(Server* sv, ServeReq* q, const StepOutcome& o, bool last) {
+  q->it_comp += o.iters;
+  q->cur ^= 1;
+  q->resumed = true;
+  q->res.last_delta = o.delta;
+  if (o.status != MAPI_OK) {
+    q->res.iters[q->comp] = q->it_comp;
+    finish(sv, q, (mapi_status)o.status);
+    return true;
+  }
+  const bool converged = q->r.tol_l1 > 0 && o.delta < (float)q->r.tol_l1;
+  if (!converged && q->it_comp < q->r.max_iters) return false;
+  if (converged && !last && o.converged_early) {
+    k_l2_normalize<<<1, 1024, 0, sv->child->stream>>>(q->wb[q->cur], q->n);
+    if (cudaGetLastError() != cudaSuccess) {
+      finish(sv, q, MAPI_ECUDA);
+      return true;
+    }
+  }
+  bool all = false;
+  const mapi_status cs = component_done(sv, q, &all);
+  if (cs != MAPI_OK || all) {
+    finish(sv, q, cs);
+    return true;
+  }
+  return false;
+}
+
+// One round over every resident solve: the wide ones on the loop's stream,
+// one after another on the whole GPU; the rest in one batched launch per
+// (storage, op) on a second stream at the same time.
 void run_round(Server* sv) {
   mapi_ctx* c = sv->child;
-  // group by (storage, op): one launch each
+  std::vector<ServeReq*> wide;
   std::map<std::pair<int, int>, std::vector<ServeReq*>> groups;
-  for (ServeReq* q : sv->live) groups[{(int)q->st, (int)q->r.op}].push_back(q);
+  for (ServeReq* q : sv->live) {
+    if (q->n >= kWideN) wide.push_back(q);
+    else groups[{(int)q->st, (int)q->r.op}].push_back(q);
+  }
+  auto steps_of = [](const ServeReq* q) {
+    const int rem = q->r.max_iters - q->it_comp;
+    return rem < kRoundSteps ? rem : kRoundSteps;
+  };
+  // deflations and copies that ended the previous round ran on the loop's
+  // stream: the batched launches of this round come after them
+  if (cudaEventRecord(sv->round_start, c->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(sv->batch_stream, sv->round_start, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(c->stream);
+  }
+  std::vector<mapi_status> wide_err(wide.size(), MAPI_OK);
+  if ((int)wide.size() > sv->wide_cap) {
+    if (sv->wide_ctl) cudaFreeHost(sv->wide_ctl);
+    sv->wide_cap = (int)wide.size() * 2;
+    if (cudaMallocHost(&sv->wide_ctl, sizeof(IterCtl) * sv->wide_cap) != cudaSuccess) {
+      cudaGetLastError();
+      sv->wide_ctl = nullptr;
+      sv->wide_cap = 0;
+    }
+  }
+  for (size_t i = 0; i < wide.size(); ++i) {
+    ServeReq* q = wide[i];
+    if (!sv->wide_ctl) {
+      wide_err[i] = MAPI_ENOMEM;
+      continue;
+    }
+    const int steps = steps_of(q);
+    const bool last = steps == q->r.max_iters - q->it_comp;
+    const unsigned flags = (q->resumed ? MAPI_FLAG_RAW_START : 0u) | (last ? MAPI_FLAG_FINAL_L2 : 0u);
+    const float* w0 = q->resumed ? q->wb[q->cur] : q->w0 + (size_t)q->comp * q->n;
+    mapi_status s = prepare_solve(c, &q->view, 1);
+    if (s == MAPI_OK)
+      s = enqueue_solve(c, c->stream, &q->view, q->r.op, 1, w0, q->n, steps, q->r.tol_l1, flags,
+                        q->wb[q->cur ^ 1], q->n);
+    if (s == MAPI_OK && cudaMemcpyAsync(&sv->wide_ctl[i], c->ctl.p, sizeof(IterCtl),
+                                        cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      s = MAPI_ECUDA;
+    }
+    wide_err[i] = s;
+  }
   std::vector<ServeReq*> ended;
   for (auto& kv : groups) {
     std::vector<ServeReq*>& qs = kv.second;
     std::vector<BatchDev> items(qs.size());
     for (size_t i = 0; i < qs.size(); ++i) {
       ServeReq* q = qs[i];
-      const int rem = q->r.max_iters - q->it_comp;
-      const int steps = rem < kRoundSteps ? rem : kRoundSteps;
+      const int steps = steps_of(q);
       BatchDev& b = items[i];
       b.A = q->A;
       b.row_bytes = q->row_bytes;
@@ -281,13 +393,12 @@ void run_round(Server* sv) {
       b.tol = (float)q->r.tol_l1;
       b.raw_start = q->resumed ? 1 : 0;
       b.final_l2 = 1;
-      b.last = steps == rem ? 1 : 0;
+      b.last = steps == q->r.max_iters - q->it_comp ? 1 : 0;
     }
     std::vector<int> res;
     std::vector<float> dl;
-    mapi_status s =
-        batched_run(c, c->stream, items, (mapi_op)kv.first.second, (mapi_storage)kv.first.first,
-                    1, res, dl);
+    const mapi_status s = batched_run(c, sv->batch_stream, items, (mapi_op)kv.first.second,
+                                      (mapi_storage)kv.first.first, 1, res, dl);
     for (size_t i = 0; i < qs.size(); ++i) {
       ServeReq* q = qs[i];
       if (s != MAPI_OK) {
@@ -295,27 +406,35 @@ void run_round(Server* sv) {
         ended.push_back(q);
         continue;
       }
-      const int it = res[2 * i], stv = res[2 * i + 1];
-      q->it_comp += it;
-      q->cur ^= 1;
-      q->resumed = true;
-      q->res.last_delta = dl[i];
-      if (stv != MAPI_OK) {
-        q->res.iters[q->comp] = q->it_comp;
-        finish(sv, q, (mapi_status)stv);
-        ended.push_back(q);
-        continue;
-      }
-      const bool converged = q->r.tol_l1 > 0 && dl[i] < (float)q->r.tol_l1;
-      if (converged || q->it_comp >= q->r.max_iters) {
-        bool all = false;
-        mapi_status cs = component_done(sv, q, &all);
-        if (cs != MAPI_OK || all) {
-          finish(sv, q, cs);
-          ended.push_back(q);
-        }
-      }
+      StepOutcome o;
+      o.iters = res[2 * i];
+      o.status = res[2 * i + 1];
+      o.delta = dl[i];
+      // the batched kernel itself applies the l2 step when the stop rule ends a solve
+      if (absorb(sv, q, o, true)) ended.push_back(q);
     }
+  }
+  if (!wide.empty() && cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    for (auto& e : wide_err)
+      if (e == MAPI_OK) e = MAPI_ECUDA;
+  }
+  for (size_t i = 0; i < wide.size(); ++i) {
+    ServeReq* q = wide[i];
+    if (wide_err[i] != MAPI_OK) {
+      finish(sv, q, wide_err[i]);
+      ended.push_back(q);
+      continue;
+    }
+    const int steps = steps_of(q);
+    const bool last = steps == q->r.max_iters - q->it_comp;
+    const VecState& v = sv->wide_ctl[i].v[0];
+    StepOutcome o;
+    o.iters = v.iters;
+    o.status = v.status;
+    o.delta = v.delta;
+    o.converged_early = v.iters < steps;
+    if (absorb(sv, q, o, last)) ended.push_back(q);
   }
   if (!ended.empty()) {
     std::vector<ServeReq*> keep;
@@ -352,6 +471,12 @@ void loop(Server* sv) {
     for (ServeReq* q : admit) {
       q->t_admit = Clock::now();
       const mapi_status s = build(sv, q);
+      if (s == MAPI_OK && cudaStreamSynchronize(sv->child->stream) != cudaSuccess) {
+        cudaGetLastError();
+        finish(sv, q, MAPI_ECUDA);
+        continue;
+      }
+      q->t_built = Clock::now();
       if (s != MAPI_OK) finish(sv, q, s);
       else sv->live.push_back(q);
     }
@@ -378,6 +503,21 @@ mapi_status ensure_server(mapi_ctx* ctx, Server** out) {
     if (s != MAPI_OK) {
       delete sv;
       return s;
+    }
+    {
+      int prev = 0;
+      cudaGetDevice(&prev);
+      cudaSetDevice(ctx->device);
+      cudaError_t e = cudaStreamCreateWithFlags(&sv->batch_stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&sv->round_start, cudaEventDisableTiming);
+      cudaSetDevice(prev);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        mapi_destroy(sv->child);
+        delete sv;
+        return MAPI_ECUDA;
+      }
     }
     sv->child->batch_rows_per_warp[0][0] = ctx->batch_rows_per_warp[0][0];
     sv->child->batch_rows_per_warp[1][0] = ctx->batch_rows_per_warp[1][0];
@@ -415,6 +555,9 @@ void server_shutdown(mapi_ctx* ctx) {
   sv->cv.notify_all();
   if (sv->th.joinable()) sv->th.join();
   for (auto& kv : sv->tickets) delete kv.second;
+  if (sv->round_start) cudaEventDestroy(sv->round_start);
+  if (sv->batch_stream) cudaStreamDestroy(sv->batch_stream);
+  if (sv->wide_ctl) cudaFreeHost(sv->wide_ctl);
   mapi_destroy(sv->child);
   delete sv;
 }

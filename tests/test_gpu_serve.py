@@ -109,15 +109,19 @@ def test_served_small_cases_equal_the_oracle(mapi_ctx):
     assert rel_l1(res[t2]["out"], want) <= TOL32
 
 
-def test_stop_rule_and_convergence(mapi_ctx):
-    ip, ix, w0 = pr_case(600, 13)
+@pytest.mark.parametrize("n", [600, 2100])  # batched launch, whole-GPU solve
+def test_stop_rule_and_convergence(mapi_ctx, n):
+    ip, ix, w0 = pr_case(n, 13)
     t = M.mapi_submit(mapi_ctx, "pagerank", w0, op="min1", storage="f32", max_iters=1000,
                       tol_l1=1e-7, indptr=ip, indices=ix)
     r = wait(mapi_ctx, [t])[t]
-    _, it, dl = M.mapi_pagerank(mapi_ctx, to_dev(ip), to_dev(ix), 600, to_dev(w0), 1000,
-                                tol_l1=1e-7)
+    want, it, dl = M.mapi_pagerank(mapi_ctx, to_dev(ip), to_dev(ix), n, to_dev(w0), 1000,
+                                   tol_l1=1e-7)
     assert r["status"] == 0 and r["last_delta"] < 1e-7
     assert r["iters"][0] < 1000 and abs(r["iters"][0] - it) <= 1
+    # the result is l2-normalised even when the stop rule ends a round early
+    assert abs(float(np.linalg.norm(r["out"].astype(np.float64))) - 1.0) < 1e-5
+    assert rel_l1(r["out"], to_host(want)) <= 1e-5
 
 
 def test_budget_rejects_what_can_never_fit():
