@@ -141,6 +141,16 @@ def make_inputs(rank: int):
     return X, W0
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest of every rank's value (the job's time is its slowest rank)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args, rank, world, local_rank, dist):
     import torch
 
@@ -189,11 +199,7 @@ def run_gpu(args, rank, world, local_rank, dist):
     clocks = sampler.stop()
     launches = M.mapi_get_stats(ctx, reset=True)["launches"]
     ms = e0.elapsed_time(e1)
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, dist, dev)
     # kernel durations: the same K steps again with CUDA events recorded on
     # the launching stream around every launch of the timed kernel classes
     M.mapi_profile(ctx, True)
@@ -243,11 +249,7 @@ def run_gpu(args, rank, world, local_rank, dist):
         step(Xh)
         _ = P.cpu()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e = {"value": round(K_COMP * ITERS * e2e_steps * world / e2e_s, 1), "unit": UNIT,
            "h2d_bytes_per_step": xbytes, "d2h_bytes_per_step": K_COMP * D * 4}
 
