@@ -329,6 +329,9 @@ mapi_status mapi_create(const mapi_config* cfg, mapi_ctx** out) {
   ctx->device = cfg->device;
   DeviceGuard g(ctx->device);
   cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device);
+  ctx->l2_bytes = (size_t)l2;
   if (cfg->cuda_stream) {
     ctx->stream = (cudaStream_t)cfg->cuda_stream;
   } else {

@@ -103,6 +103,7 @@ struct Server;
 struct mapi_ctx {
   int device = 0;
   int sm_count = 0;
+  size_t l2_bytes = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t hbm_budget = 0;

@@ -370,92 +370,99 @@ struct PairArgs {
   DeflArgs defl;
   int norm_l2;
   float denom;
+  int reverse;    // walk this cluster's tiles last to first (odd steps), so a
+                  // step starts on the tiles the previous one read last and
+                  // that are still in L2
+  int keep_tiles; // this many of a cluster's last tiles are kept in L2
 };
 
 // Floats of shared memory the last cluster's epilogue needs: ys, u, wo (own
 // rows), yfull and cbuf (D_pad each), four scan buffers and the component's
 // w, sorted c, perm and ub (kDeflMaxD each).
+// one padded array of the deflation: kDeflMaxD entries, one spare word per 32
+constexpr int kDeflPadded = kDeflMaxD + kDeflMaxD / 32;
 __host__ __device__ constexpr int pair_epi_floats(int rc, int d_pad) {
-  return 3 * rc + 2 * d_pad + 8 * kDeflMaxD;
+  return 3 * rc + 3 * d_pad + 2 * 8 * kDeflPadded;
 }
+
+constexpr int kPairMaxClusters = 80;  // partials per row the epilogue reads at once
+constexpr int kEpiHalf = kPairWarps * 32 / 2;  // threads that load one component
+
+// Index of sorted position p in a padded deflation array: lane l's run of
+// 32 positions [32 l, 32 l + 32) then falls on 32 different banks.
+__device__ __forceinline__ int dpad(int p) { return p + (p >> 5); }
 
 // Epilogue of one pair step, run by the last cluster to finish: CTA r owns
 // rows [r*RS, (r+1)*RS) (the rows it streamed).  y = sum of the cluster
-// partials (fixed order) / denom; u = y - sum_m P_m y (prefix-sum form,
-// components spread over the 4 CTAs); w_next = u / ||u||_1 (||u||_2 for
-// DOT); delta and the stop test.  Shared memory: the (now idle) stage ring.
+// partials (fixed order) / denom; u = y - sum_m P_m y (prefix-sum form; warps
+// 0 and 1 of every CTA each take one earlier component, so up to 8 run at
+// once, each scanned by one warp without block barriers); w_next =
+// u / ||u||_1 (||u||_2 for DOT); delta and the stop test.  Shared memory: the
+// (now idle) stage ring.
 template <int RS>
 __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, float* fsh) {
   constexpr int CS = kPairCluster;
   constexpr int NT = kPairWarps * 32;
-  constexpr int PER = kDeflMaxD / NT;
   const int r = (int)cluster.block_rank();
   const int r0 = r * RS;
   const int D = a.D;
+  const int h = threadIdx.x / kEpiHalf;  // half that loads component r + CS h
+  const int th = threadIdx.x % kEpiHalf;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* ys = fsh;
   float* u = ys + RS;
   float* wo = u + RS;
   float* yfull = wo + RS;
-  float* cbuf = yfull + a.D_pad;
-  float* sA = cbuf + a.D_pad;
-  float* sB = sA + kDeflMaxD;
-  float* sA2 = sB + kDeflMaxD;
-  float* sB2 = sA2 + kDeflMaxD;
-  float* wm_s = sB2 + kDeflMaxD;
-  float* cs_s = wm_s + kDeflMaxD;
-  int* perm_s = reinterpret_cast<int*>(cs_s + kDeflMaxD);
-  int* ub_s = perm_s + kDeflMaxD;
+  float* cbuf = yfull + a.D_pad;  // [2][D_pad]: one per deflating warp
+  auto arrays = [&](int g) { return cbuf + 2 * a.D_pad + g * 8 * kDeflPadded; };
   __shared__ float red[33];
   __shared__ float part[4];
-  __shared__ float wtot[NT / 32];
-  __shared__ float dotv;
+  const bool dot = a.defl.op == MAPI_OP_DOT;
 
-  // 0. prefetch: this CTA's first component, the old iterate's own rows
-  const int m0 = r;
-  if (m0 < a.defl.nprev) {
-    const float* wm = a.defl.P + (int64_t)m0 * a.defl.ldp;
-    const bool dot = a.defl.op == MAPI_OP_DOT;
-    float w_[PER], c_[PER];
-    int p_[PER], u_[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < D) {
-        w_[k] = wm[i];
-        if (!dot) {
-          c_[k] = a.defl.csort[(int64_t)m0 * a.defl.stride + i];
-          p_[k] = a.defl.perm[(int64_t)m0 * a.defl.stride + i];
-          u_[k] = a.defl.ubi[(int64_t)m0 * a.defl.stride + i];
-        }
+  // component m's vector, sorted |w| and the two index maps into group g's
+  // padded arrays, loaded by the threads [t0, t0 + nt)
+  auto load_comp = [&](int m, int g, int t, int nt) {
+    const float* wm = a.defl.P + (int64_t)m * a.defl.ldp;
+    float* wm_s = arrays(g) + 4 * kDeflPadded;
+    float* cs_s = wm_s + kDeflPadded;
+    int* perm_s = reinterpret_cast<int*>(cs_s + kDeflPadded);
+    int* ub_s = perm_s + kDeflPadded;
+    const int64_t o = (int64_t)m * a.defl.stride;
+    for (int i = t; i < D; i += nt) {
+      wm_s[i] = wm[i];
+      if (!dot) {
+        cs_s[dpad(i)] = a.defl.csort[o + i];
+        perm_s[dpad(i)] = a.defl.perm[o + i];
+        ub_s[i] = a.defl.ubi[o + i];
       }
     }
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < D) {
-        wm_s[i] = w_[k];
-        if (!dot) {
-          cs_s[i] = c_[k];
-          perm_s[i] = p_[k];
-          ub_s[i] = u_[k];
-        }
-      }
-    }
-  }
-  // 1. own rows of y: one row per thread, the row's cluster partials read as
-  //    float4 and added in cluster order
+  };
+  // 0. prefetch: the first component of each deflating warp
+  if (r + CS * h < a.defl.nprev) load_comp(r + CS * h, h, th, kEpiHalf);
+  // 1. own rows of y: one row per thread; the row's cluster partials are all
+  //    loaded before any is added (in cluster order)
   for (int i = threadIdx.x; i < RS; i += NT) {
     const int d = r0 + i;
     wo[i] = d < D ? a.w[d] : 0.f;
     const float4* src = reinterpret_cast<const float4*>(a.ypart + (int64_t)d * a.pstride);
+    const int p4 = a.pstride / 4;
+    constexpr int B4 = kPairMaxClusters / 8;  // two batches of loads in flight
     float sum = 0.f;
-#pragma unroll 8
-    for (int g4 = 0; g4 < a.pstride / 4; ++g4) {
-      const float4 v = src[g4];
-      sum += v.x;
-      sum += v.y;
-      sum += v.z;
-      sum += v.w;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      float4 v[B4];
+#pragma unroll
+      for (int g = 0; g < B4; ++g)
+        v[g] = b * B4 + g < p4 ? src[b * B4 + g] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int g = 0; g < B4; ++g) {
+        if (b * B4 + g < p4) {
+          sum += v[g].x;
+          sum += v[g].y;
+          sum += v[g].z;
+          sum += v[g].w;
+        }
+      }
     }
     ys[i] = d < D ? sum / a.denom : 0.f;
   }
@@ -463,83 +470,118 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
   // 2. deflation
   if (a.defl.nprev > 0) {
     cluster.sync();
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < a.D_pad) {
-        yfull[i] = cluster.map_shared_rank(ys, i / RS)[i % RS];
-        cbuf[i] = 0.f;
-      }
+    for (int i = threadIdx.x; i < a.D_pad; i += NT) {
+      yfull[i] = cluster.map_shared_rank(ys, i / RS)[i % RS];
+      cbuf[i] = 0.f;
+      cbuf[a.D_pad + i] = 0.f;
     }
     __syncthreads();
-    for (int m = m0; m < a.defl.nprev; m += CS) {
-      const float* wm = a.defl.P + (int64_t)m * a.defl.ldp;
-      if (m != m0) {  // more components than CTAs
-        for (int i = threadIdx.x; i < D; i += NT) {
-          wm_s[i] = wm[i];
-          if (a.defl.op != MAPI_OP_DOT) {
-            cs_s[i] = a.defl.csort[(int64_t)m * a.defl.stride + i];
-            perm_s[i] = a.defl.perm[(int64_t)m * a.defl.stride + i];
-            ub_s[i] = a.defl.ubi[(int64_t)m * a.defl.stride + i];
+    if (warp < 2) {
+      float* cb = cbuf + warp * a.D_pad;
+      float* sA = arrays(warp);
+      float* sB = sA + kDeflPadded;
+      float* sA2 = sB + kDeflPadded;
+      float* sB2 = sA2 + kDeflPadded;
+      const float* wm_s = sB2 + kDeflPadded;
+      const float* cs_s = wm_s + kDeflPadded;
+      const int* perm_s = reinterpret_cast<const int*>(cs_s + kDeflPadded);
+      const int* ub_s = perm_s + kDeflPadded;
+      const bool two = a.defl.op == MAPI_OP_MIN2;
+      for (int m = r + CS * warp; m < a.defl.nprev; m += 2 * CS) {
+        if (m >= 2 * CS) {  // more components than deflating warps
+          __syncwarp();
+          load_comp(m, warp, lane, 32);
+        }
+        __syncwarp();
+        if (dot) {
+          float pd = 0.f;
+          for (int i = lane; i < D; i += 32) pd += wm_s[i] * yfull[i];
+#pragma unroll
+          for (int o = 16; o; o >>= 1) pd += __shfl_xor_sync(0xffffffffu, pd, o);
+          for (int i = lane; i < D; i += 32) cb[i] += wm_s[i] * pd;
+          continue;
+        }
+        // lane l scans the sorted positions [32 l, 32 l + 32)
+        float ra = 0.f, rb = 0.f, ra2 = 0.f, rb2 = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+          const int p = lane * 32 + k;
+          if (p < D) {
+            const int i = perm_s[dpad(p)];
+            const float y = yfull[i];
+            const float c = cs_s[dpad(p)];
+            const float z = sgnf(wm_s[i]) * y;
+            ra += c * z;
+            rb += z;
+            sA[dpad(p)] = ra;
+            sB[dpad(p)] = rb;
+            if (two) {
+              ra2 += c * y;
+              rb2 += y;
+              sA2[dpad(p)] = ra2;
+              sB2[dpad(p)] = rb2;
+            }
           }
         }
-        __syncthreads();
-      }
-      if (a.defl.op == MAPI_OP_DOT) {
-        Kahan kd;
-        for (int i = threadIdx.x; i < D; i += NT) kd.add(wm_s[i] * yfull[i]);
-        const float dv = block_sum<NT>(kd.value(), red);
-        if (threadIdx.x == 0) dotv = dv;
-        __syncthreads();
-        for (int i = threadIdx.x; i < D; i += NT) cbuf[i] += wm_s[i] * dotv;
-        __syncthreads();
-        continue;
-      }
-      const bool two = a.defl.op == MAPI_OP_MIN2;
+        // exclusive offsets of the lanes' runs
+        float oa = ra, ob = rb, oa2 = ra2, ob2 = rb2;
 #pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const int p = threadIdx.x + k * NT;
-        float z = 0.f, y = 0.f, c = 0.f;
-        if (p < D) {
-          const int i = perm_s[p];
-          y = yfull[i];
-          z = sgnf(wm_s[i]) * y;
-          c = cs_s[p];
+        for (int o = 1; o < 32; o <<= 1) {
+          const float na = __shfl_up_sync(0xffffffffu, oa, o);
+          const float nb = __shfl_up_sync(0xffffffffu, ob, o);
+          const float na2 = __shfl_up_sync(0xffffffffu, oa2, o);
+          const float nb2 = __shfl_up_sync(0xffffffffu, ob2, o);
+          if (lane >= o) {
+            oa += na;
+            ob += nb;
+            oa2 += na2;
+            ob2 += nb2;
+          }
         }
-        sA[p] = c * z;
-        sB[p] = z;
-        if (two) {
-          sA2[p] = c * y;
-          sB2[p] = y;
+        const float totB = __shfl_sync(0xffffffffu, ob, 31);
+        const float totB2 = __shfl_sync(0xffffffffu, ob2, 31);
+        oa -= ra;
+        ob -= rb;
+        oa2 -= ra2;
+        ob2 -= rb2;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+          const int p = lane * 32 + k;
+          if (p < D) {
+            sA[dpad(p)] += oa;
+            sB[dpad(p)] += ob;
+            if (two) {
+              sA2[dpad(p)] += oa2;
+              sB2[dpad(p)] += ob2;
+            }
+          }
+        }
+        __syncwarp();
+        for (int i = lane; i < D; i += 32) {
+          const float wi = wm_s[i], ci = fabsf(wi);
+          const int q = dpad(ub_s[i]);
+          float v = sgnf(wi) * (sA[q] + ci * (totB - sB[q]));
+          if (two) v = 0.5f * (v + (sA2[q] + ci * (totB2 - sB2[q])));
+          cb[i] += v;
         }
       }
-      __syncthreads();
-      block_scan4<NT>(sA, wtot);
-      block_scan4<NT>(sB, wtot);
-      if (two) {
-        block_scan4<NT>(sA2, wtot);
-        block_scan4<NT>(sB2, wtot);
-      }
-      const float totB = sB[D - 1], totB2 = two ? sB2[D - 1] : 0.f;
-      for (int i = threadIdx.x; i < D; i += NT) {
-        const float wi = wm_s[i], ci = fabsf(wi);
-        const int q = ub_s[i];
-        float v = sgnf(wi) * (sA[q] + ci * (totB - sB[q]));
-        if (two) v = 0.5f * (v + (sA2[q] + ci * (totB2 - sB2[q])));
-        cbuf[i] += v;
-      }
-      __syncthreads();
     }
     cluster.sync();
     const int nq = min(CS, a.defl.nprev);
+    const bool second = a.defl.nprev > CS;  // some CTA's second warp holds a sum
     for (int i = threadIdx.x; i < RS; i += NT) {
       const int d = r0 + i;
-      float v[CS];
+      float v[2 * CS];
 #pragma unroll
-      for (int q = 0; q < CS; ++q) v[q] = q < nq ? cluster.map_shared_rank(cbuf, q)[d] : 0.f;
+      for (int q = 0; q < CS; ++q) {
+        const float* cq = cluster.map_shared_rank(cbuf, q);
+        v[q] = q < nq ? cq[d] : 0.f;
+        v[CS + q] = second ? cq[a.D_pad + d] : 0.f;
+      }
+      // components in order m = 0, 1, ..., 2 CS - 1
       float sub = 0.f;
 #pragma unroll
-      for (int q = 0; q < CS; ++q) sub += v[q];
+      for (int q = 0; q < 2 * CS; ++q) sub += v[q];
       u[i] = d < D ? ys[i] - sub : 0.f;
     }
   } else {
@@ -628,17 +670,25 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // the tiles read last stay in L2 for the next step (which walks the other
+  // way); the others leave L2 first
+  const uint64_t pol_first = createpolicy_evict_first();
+  const uint64_t pol_last = createpolicy_evict_last();
   auto issue = [&](int j) {
     const int s = j % kPairStages;
-    const int tile = cid + j * a.nclusters;
+    const int tile = cid + (a.reverse ? nmine - 1 - j : j) * a.nclusters;
     mbar_expect_tx(&full[s], kStageBytes);
-    tma_load_2d(stage + (size_t)s * RC * 32, &xmap, tile * TC, (int)crank * RC, &full[s]);
+    tma_load_2d_hint(stage + (size_t)s * RC * 32, &xmap, tile * TC, (int)crank * RC, &full[s],
+                     j >= nmine - a.keep_tiles ? pol_last : pol_first);
   };
   // X does not depend on the previous step: start streaming it before waiting
   // for that step (programmatic dependent launch)
   const int npre = nmine < kPairStages ? nmine : kPairStages;
   if (threadIdx.x == 0)
     for (int j = 0; j < npre; ++j) issue(j);
+  // peers push into tin / tready only after every CTA of the cluster has
+  // initialised its barriers; this wait needs nothing from the previous step
+  cluster.sync();
   cudaGridDependencySynchronize();
   if (*(volatile const int*)&a.ctl->all_done) {
     // nothing left to do: let the copies already issued land, then leave
@@ -655,8 +705,6 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
     else wp[r] = make_float4(p.lo, p.hi, p.s, 0.f);
   }
   __syncthreads();
-  // peers push into tin / tready only after the cluster has started
-  cluster.sync();
 
   float acc[RW];
 #pragma unroll
@@ -746,13 +794,31 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
   } else if (nmine > 0) {
     phase_b(nmine - 1, rawB);
   }
-  // row sums across the 32 lanes, written once per cluster
+  // row sums across the 32 lanes, written once per cluster: a transposing
+  // butterfly halves the rows each lane holds at every level (31 shuffles
+  // for 32 rows), so lane l ends with row l / (32 / RW)
+  {
+    constexpr int H = RW == 32 ? 5 : RW == 16 ? 4 : RW == 8 ? 3 : -1;
+    static_assert(H > 0, "RW must be 8, 16 or 32");
 #pragma unroll
-  for (int jj = 0; jj < RW; ++jj) {
-    float sum = acc[jj];
+    for (int lev = 0; lev < 5; ++lev) {
+      const int o = 16 >> lev;
+      if (lev < H) {
+        const int half = RW >> (lev + 1);
+        const bool upper = (lane & o) != 0;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) a.ypart[(int64_t)(rbase + jj) * a.pstride + cid] = sum;
+        for (int k = 0; k < half; ++k) {
+          const float send = upper ? acc[k] : acc[k + half];
+          const float keep = upper ? acc[k + half] : acc[k];
+          acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      } else {
+        acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+      }
+    }
+    constexpr int grp = 32 / RW;
+    if ((lane & (grp - 1)) == 0)
+      a.ypart[(int64_t)(rbase + lane / grp) * a.pstride + cid] = acc[0];
   }
   if (threadIdx.x == 0 && s_err) {
     // a tile or a peer's partials never arrived: report it; the solve stops
@@ -938,17 +1004,29 @@ static mapi_status plan_pair(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, PairL
   if (nclusters < 1) return fail(ctx, MAPI_ECUDA, "pair kernel: no cluster fits");
   pl->fn = fn;
   pl->rw = rw;
-  pl->clusters = nclusters;
+  pl->clusters = std::min(nclusters, kPairMaxClusters);
   return MAPI_OK;
 }
 
 static int pair_pstride(int nclusters) { return (nclusters + 3) / 4 * 4; }
 
+// Tiles per cluster whose lines are kept in L2 for the next step: together
+// they fill about 60 % of L2 (the rest: stages, partials and the data of
+// other streams).  When that covers all of a cluster's tiles, X stays in L2.
+static int pair_keep_tiles(const mapi_ctx* ctx, const mapi_mat* X, const PairLaunch& pl) {
+  const int TC = (X->storage == MAPI_ST_F32) ? 32 : 64;
+  const double tile_bytes = (double)kPairCluster * kPairWarps * pl.rw * TC * elem_bytes(X->storage);
+  const double keep = 0.6 * ctx->l2_bytes / (tile_bytes * pl.clusters);
+  return keep < 0 ? 0 : (int)keep;
+}
+
 static mapi_status launch_pair_step(mapi_ctx* ctx, cudaStream_t s, const PairLaunch& pl,
                                     const mapi_mat* X, const float* w, float* w_next,
                                     float* ypart, const DeflArgs& defl, IterCtl* ctl,
-                                    int norm_l2, float denom) {
+                                    int norm_l2, float denom, int reverse) {
   PairArgs pa;
+  pa.reverse = reverse;
+  pa.keep_tiles = pair_keep_tiles(ctx, X, pl);
   pa.D = X->rows;
   const int TC = (X->storage == MAPI_ST_F32) ? 32 : 64;
   pa.ntiles = (int)((X->ld + TC - 1) / TC);
@@ -1094,8 +1172,9 @@ mapi_status pca_enqueue(mapi_ctx* ctx, cudaStream_t s, const mapi_mat* X, const 
     for (int t = 0; t < p.iters; ++t) {
       const float* wc = (t & 1) ? wb1 : wb0;
       float* wn = (t & 1) ? wb0 : wb1;
+      // the tile order alternates over all steps of all components
       if ((st = launch_pair_step(ctx, s, p.pl, X, wc, wn, (float*)ctx->ypart.p, defl, ctl,
-                                 norm_l2, (float)p.denom)) != MAPI_OK)
+                                 norm_l2, (float)p.denom, (c * p.iters + t) & 1)) != MAPI_OK)
         return st;
     }
     if ((st = launch_finish(ctx, s, wb0, wb1, p.wst, D, 1, ctl, 1, 0, 0, P_out + (int64_t)c * D,
