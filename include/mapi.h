@@ -259,8 +259,10 @@ mapi_status mapi_pagerank(mapi_ctx* ctx, const int* indptr, const int* indices,
 /* Kernel classes timed by mapi_profile. */
 typedef enum {
   MAPI_KC_GEMV = 0,        /* K1 MAVP-GEMV step (Alg. 1 steps 3-4) */
-  MAPI_KC_PAIR = 1,        /* pair-step partials over X */
-  MAPI_KC_PAIR_FINISH = 2, /* pair-step reduction, deflation, normalisation */
+  MAPI_KC_PAIR = 1,        /* pair step over X, its reduction, deflation and
+                              normalisation included (one kernel) */
+  MAPI_KC_PAIR_FINISH = 2, /* reserved: the pair step has no separate finish
+                              kernel, so this class stays empty */
   MAPI_KC_MINCOV = 3,      /* min-covariance build, Eq. (5) */
   MAPI_KC_BATCHED = 4,     /* persistent batched solve (whole launch) */
   MAPI_KC_COUNT = 5
