@@ -35,17 +35,41 @@ constexpr int kEpiThreads = 256;
 // Last-CTA epilogue for float storage.  NT threads.
 template <int NT, int V>
 __device__ void epilogue_float(const GemvArgs& g, int ks) {
+  constexpr int kEpiU = 8;
   __shared__ float sh[33];
   for (int v = 0; v < V; ++v) {
     VecState* st = &g.ctl->v[v];
     if (*(volatile int*)&st->done) continue;  // uniform: written by earlier launches
     float* y0 = g.ypart + (int64_t)v * g.rows_pad;
+    // kEpiU rows per thread in flight (the same order of additions as one at
+    // a time): one CTA runs this for all n rows, so its loads must overlap
     Kahan acc;
-    for (int i = threadIdx.x; i < g.n; i += NT) {
-      float yi = __ldcg(y0 + i);
-      for (int k = 1; k < ks; ++k) yi += __ldcg(g.ypart + ((int64_t)k * V + v) * g.rows_pad + i);
-      if (ks > 1) y0[i] = yi;
-      acc.add(g.norm_l2 ? yi * yi : fabsf(yi));
+    for (int i0 = threadIdx.x; i0 < g.n; i0 += NT * kEpiU) {
+      float yv[kEpiU];
+#pragma unroll
+      for (int u = 0; u < kEpiU; ++u) {
+        const int i = i0 + u * NT;
+        yv[u] = i < g.n ? __ldcg(y0 + i) : 0.f;
+      }
+      for (int k = 1; k < ks; ++k) {
+        const float* yk = g.ypart + ((int64_t)k * V + v) * g.rows_pad;
+        float pk[kEpiU];
+#pragma unroll
+        for (int u = 0; u < kEpiU; ++u) {
+          const int i = i0 + u * NT;
+          pk[u] = i < g.n ? __ldcg(yk + i) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kEpiU; ++u) yv[u] += pk[u];
+      }
+#pragma unroll
+      for (int u = 0; u < kEpiU; ++u) {
+        const int i = i0 + u * NT;
+        if (i < g.n) {
+          if (ks > 1) y0[i] = yv[u];
+          acc.add(g.norm_l2 ? yv[u] * yv[u] : fabsf(yv[u]));
+        }
+      }
     }
     float L = block_sum<NT>(acc.value(), sh);
     if (g.norm_l2) L = sqrtf(L);
@@ -59,11 +83,23 @@ __device__ void epilogue_float(const GemvArgs& g, int ks) {
     const float* wo = g.w + (int64_t)v * g.wst;
     float* wn = g.w_next + (int64_t)v * g.wst;
     Kahan dl;
-    for (int i = threadIdx.x; i < g.n; i += NT) {
-      const float yi = (ks > 1) ? y0[i] : __ldcg(y0 + i);
-      const float x = yi / L;  // the n divisions of §2.2
-      dl.add(fabsf(x - wo[i]));
-      wn[i] = x;
+    for (int i0 = threadIdx.x; i0 < g.n; i0 += NT * kEpiU) {
+      float yv[kEpiU], wv[kEpiU];
+#pragma unroll
+      for (int u = 0; u < kEpiU; ++u) {
+        const int i = i0 + u * NT;
+        yv[u] = i < g.n ? ((ks > 1) ? y0[i] : __ldcg(y0 + i)) : 0.f;
+        wv[u] = i < g.n ? wo[i] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kEpiU; ++u) {
+        const int i = i0 + u * NT;
+        if (i < g.n) {
+          const float x = yv[u] / L;  // the n divisions of §2.2
+          dl.add(fabsf(x - wv[u]));
+          wn[i] = x;
+        }
+      }
     }
     const float D = block_sum<NT>(dl.value(), sh);
     if (threadIdx.x == 0) {
@@ -180,6 +216,7 @@ struct IGemvArgs {
 
 template <int NT, int V>
 __device__ void epilogue_int(const IGemvArgs& a, int ks) {
+  constexpr int kEpiU = 8;  // rows per thread in flight (see epilogue_float)
   const GemvArgs& g = a.g;
   __shared__ long long sh[33];
   const int* ypart = reinterpret_cast<const int*>(g.ypart);
@@ -188,11 +225,32 @@ __device__ void epilogue_int(const IGemvArgs& a, int ks) {
     if (*(volatile int*)&st->done) continue;
     int* y0 = reinterpret_cast<int*>(g.ypart) + (int64_t)v * g.rows_pad;
     long long s = 0;
-    for (int i = threadIdx.x; i < g.n; i += NT) {
-      int yi = __ldcg(y0 + i);
-      for (int k = 1; k < ks; ++k) yi += __ldcg(ypart + ((int64_t)k * V + v) * g.rows_pad + i);
-      if (ks > 1) y0[i] = yi;
-      s += (long long)abs(yi);
+    for (int i0 = threadIdx.x; i0 < g.n; i0 += NT * kEpiU) {
+      int yv[kEpiU];
+#pragma unroll
+      for (int u = 0; u < kEpiU; ++u) {
+        const int i = i0 + u * NT;
+        yv[u] = i < g.n ? __ldcg(y0 + i) : 0;
+      }
+      for (int k = 1; k < ks; ++k) {
+        const int* yk = ypart + ((int64_t)k * V + v) * g.rows_pad;
+        int pk[kEpiU];
+#pragma unroll
+        for (int u = 0; u < kEpiU; ++u) {
+          const int i = i0 + u * NT;
+          pk[u] = i < g.n ? __ldcg(yk + i) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kEpiU; ++u) yv[u] += pk[u];
+      }
+#pragma unroll
+      for (int u = 0; u < kEpiU; ++u) {
+        const int i = i0 + u * NT;
+        if (i < g.n) {
+          if (ks > 1) y0[i] = yv[u];
+          s += (long long)abs(yv[u]);
+        }
+      }
     }
     const long long L = block_sum_i64<NT>(s, sh);
     if (L == 0) {
@@ -206,12 +264,24 @@ __device__ void epilogue_int(const IGemvArgs& a, int ks) {
     int* wn = reinterpret_cast<int*>(g.w_next) + (int64_t)v * g.wst;
     long long d = 0;
     const long long half = L / 2;
-    for (int i = threadIdx.x; i < g.n; i += NT) {
-      const int yi = (ks > 1) ? y0[i] : __ldcg(y0 + i);
-      const long long m = (((long long)abs(yi) << a.q) + half) / L;
-      const int x = yi < 0 ? -(int)m : (int)m;
-      d += (long long)abs(x - wo[i]);
-      wn[i] = x;
+    for (int i0 = threadIdx.x; i0 < g.n; i0 += NT * kEpiU) {
+      int yv[kEpiU], wv[kEpiU];
+#pragma unroll
+      for (int u = 0; u < kEpiU; ++u) {
+        const int i = i0 + u * NT;
+        yv[u] = i < g.n ? ((ks > 1) ? y0[i] : __ldcg(y0 + i)) : 0;
+        wv[u] = i < g.n ? wo[i] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kEpiU; ++u) {
+        const int i = i0 + u * NT;
+        if (i < g.n) {
+          const long long m = (((long long)abs(yv[u]) << a.q) + half) / L;
+          const int x = yv[u] < 0 ? -(int)m : (int)m;
+          d += (long long)abs(x - wv[u]);
+          wn[i] = x;
+        }
+      }
     }
     const long long D = block_sum_i64<NT>(d, sh);
     if (threadIdx.x == 0) {
