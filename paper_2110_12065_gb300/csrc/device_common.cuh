@@ -4,6 +4,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
@@ -148,6 +149,22 @@ struct Chunk<kBF16> {
 // same (exact) power-of-two factor by the caller.
 __device__ __forceinline__ float e4m3_bits_unscaled(uint32_t b) {
   return __uint_as_float(((b & 0x7Fu) << 20) | ((b & 0x80u) << 24));
+}
+
+// The four E4M3 bytes of a word (byte 0 first) as their exact values, by the
+// hardware conversion of byte pairs to f16 pairs (every E4M3 value is an f16
+// value) and of each half to f32.
+__device__ __forceinline__ void e4m3x4_values(uint32_t wd, float& f0, float& f1, float& f2,
+                                              float& f3) {
+  uint32_t lo, hi;
+  asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+      "cvt.rn.f16x2.e4m3x2 %0, l;\n\tcvt.rn.f16x2.e4m3x2 %1, h;\n\t}"
+      : "=r"(lo), "=r"(hi)
+      : "r"(wd));
+  f0 = __half2float(__ushort_as_half((unsigned short)(lo & 0xFFFFu)));
+  f1 = __half2float(__ushort_as_half((unsigned short)(lo >> 16)));
+  f2 = __half2float(__ushort_as_half((unsigned short)(hi & 0xFFFFu)));
+  f3 = __half2float(__ushort_as_half((unsigned short)(hi >> 16)));
 }
 
 template <>

@@ -138,9 +138,11 @@ __global__ void __launch_bounds__(WARPS * 32)
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[r][v][0] = acc[r][v][1] = 0.f;
 
+  // FP8: the row scale 2^k (the stored factor 2^(120 + k) serves the
+  // bit-placement decoder; the hardware conversion needs 2^-120 of it, exact)
   float mult[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) mult[r] = (ST == kFP8) ? g.row_mult[row0 + r] : 1.f;
+  for (int r = 0; r < R; ++r) mult[r] = (ST == kFP8) ? g.row_mult[row0 + r] * 0x1p-120f : 1.f;
 
   const uint8_t* arow = g.A + (int64_t)row0 * g.row_bytes;
 
@@ -157,8 +159,15 @@ __global__ void __launch_bounds__(WARPS * 32)
         const auto p3 = Op<OP>::prep(wv.w);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          float a0 = ch[r].get(grp * 4 + 0), a1 = ch[r].get(grp * 4 + 1);
-          float a2 = ch[r].get(grp * 4 + 2), a3 = ch[r].get(grp * 4 + 3);
+          float a0, a1, a2, a3;
+          if constexpr (ST == kFP8) {
+            e4m3x4_values((&ch[r].raw.x)[grp], a0, a1, a2, a3);
+          } else {
+            a0 = ch[r].get(grp * 4 + 0);
+            a1 = ch[r].get(grp * 4 + 1);
+            a2 = ch[r].get(grp * 4 + 2);
+            a3 = ch[r].get(grp * 4 + 3);
+          }
           if (ST == kFP8) {
             a0 *= mult[r];
             a1 *= mult[r];
