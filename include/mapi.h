@@ -321,7 +321,7 @@ mapi_status mapi_iterate_batched(mapi_ctx* ctx, const mapi_batch_item* items, in
 
 /*
  * Autotuner of the batched solve: times `iters` steps of the given batch
- * for each candidate rows-per-warp (1, 2, 4) and keeps the fastest for this
+ * for each candidate rows-per-warp (1, 2, 4, 8) and keeps the fastest for this
  * context, storage and vector count (*chosen receives it; may be NULL).
  * The outputs of the batch are overwritten.
  */

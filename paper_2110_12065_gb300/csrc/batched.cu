@@ -36,8 +36,8 @@ struct BatchArgs {
 };
 
 // y = A (+) w for V vectors in shared memory; a warp owns R rows at a time,
-// its lanes stride over the row's 16-byte chunks with U = 8/R chunks per row
-// in flight (the loads of a group are issued before any of it is consumed).
+// its lanes stride over the row's 16-byte chunks, the next chunk of each row
+// loading while the current one is consumed.
 // w_s is [j][V] and zero past n up to the packed row length, so the zero
 // padding of the packed rows contributes exact zeros; y_s is [i - rb][V].
 template <int OP, int ST, int V, int R>
@@ -45,7 +45,6 @@ __device__ __forceinline__ void cta_product(const BatchDev& it, const float* __r
                                             float* __restrict__ y_s, int rb, int re) {
   using Ch = Chunk<ST>;
   constexpr int E = Ch::E;
-  constexpr int U = 8 / R;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int row0 = rb + warp * R; row0 < re; row0 += kBatchWarps * R) {
     float acc[R][V];
@@ -57,41 +56,45 @@ __device__ __forceinline__ void cta_product(const BatchDev& it, const float* __r
 #pragma unroll
     for (int r = 0; r < R; ++r)
       rowp[r] = it.A + (int64_t)min(row0 + r, re - 1) * it.row_bytes;  // rows past re repeat
-    for (int c0 = lane; c0 < it.chunks; c0 += 32 * U) {
-      Ch ch[U][R];
+    auto load = [&](Ch (&dst)[R], int c) {
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+      for (int r = 0; r < R; ++r)
+        dst[r].raw = c < it.chunks ? ld_stream(rowp[r] + (int64_t)c * 16) : make_uint4(0, 0, 0, 0);
+    };
+    auto consume = [&](const Ch (&src)[R], int c) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int c = c0 + 32 * u;
-          ch[u][r].raw = c < it.chunks ? ld_stream(rowp[r] + (int64_t)c * 16) : make_uint4(0, 0, 0, 0);
+      for (int e = 0; e < E; ++e) {
+        const int j = c * E + e;
+        float wv[V];
+        if constexpr (V == 4) {
+          const float4 q = *reinterpret_cast<const float4*>(w_s + j * 4);
+          wv[0] = q.x;
+          wv[1] = q.y;
+          wv[2] = q.z;
+          wv[3] = q.w;
+        } else {
+#pragma unroll
+          for (int v = 0; v < V; ++v) wv[v] = w_s[j * V + v];
         }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int c = c0 + 32 * u;
-        if (c >= it.chunks) break;
+        for (int v = 0; v < V; ++v) {
+          const auto p = Op<OP>::prep(wv[v]);
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int j = c * E + e;
-          float wv[V];
-          if constexpr (V == 4) {
-            const float4 q = *reinterpret_cast<const float4*>(w_s + j * 4);
-            wv[0] = q.x;
-            wv[1] = q.y;
-            wv[2] = q.z;
-            wv[3] = q.w;
-          } else {
-#pragma unroll
-            for (int v = 0; v < V; ++v) wv[v] = w_s[j * V + v];
-          }
-#pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const auto p = Op<OP>::prep(wv[v]);
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r][v] = Op<OP>::term(ch[u][r].get(e), p, acc[r][v]);
-          }
+          for (int r = 0; r < R; ++r) acc[r][v] = Op<OP>::term(src[r].get(e), p, acc[r][v]);
         }
       }
+    };
+    // software pipeline: the next chunk of every row is in flight while the
+    // current one is consumed
+    Ch b0[R], b1[R];
+    int c = lane;
+    load(b0, c);
+    for (; c < it.chunks; c += 64) {
+      load(b1, c + 32);
+      consume(b0, c);
+      if (c + 32 >= it.chunks) break;
+      load(b0, c + 64);
+      consume(b1, c + 32);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -355,6 +358,7 @@ static BatchFn pick_r(int r) {
     case 1: return k_batched<OP, ST, V, 1>;
     case 2: return k_batched<OP, ST, V, 2>;
     case 4: return k_batched<OP, ST, V, 4>;
+    case 8: return k_batched<OP, ST, V, 8>;
   }
   return nullptr;
 }
@@ -573,7 +577,7 @@ extern "C" mapi_status mapi_autotune_batched(mapi_ctx* ctx, const mapi_batch_ite
   MAPI_CUDA_TRY(ctx, cudaEventCreate(&e1));
   float best = 1e30f;
   int best_r = 2;
-  for (int r : {1, 2, 4}) {
+  for (int r : {1, 2, 4, 8}) {
     *slot = r;
     mapi_status s = mapi_iterate_batched(ctx, items, count, op, nvec, 1, 0.0, MAPI_FLAG_RAW_START,
                                          nullptr, nullptr, nullptr);  // warm

@@ -79,7 +79,7 @@ def test_batched_autotune_keeps_results(mapi_ctx):
         M.mapi_iterate_batched(mapi_ctx, items, "min1", 4, 5)
         ref = [to_host(w_out).copy() for _, _, w_out in items]
         r = M.mapi_autotune_batched(mapi_ctx, items, "min1", 4, iters=2)
-        assert r in (1, 2, 4)
+        assert r in (1, 2, 4, 8)
         M.mapi_iterate_batched(mapi_ctx, items, "min1", 4, 5)
         for (_, _, w_out), want in zip(items, ref):
             assert rel_l1(to_host(w_out), want) <= TOL32
