@@ -66,6 +66,7 @@ def _get():
                 "or_pair_step": (None, [i, p, l, l, l, p, d, p]),
                 "or_pca_topk": (i, [i, i, p, l, l, l, l, i, d, d, p, l, p, l, p]),
                 "or_google_matrix": (None, [l, p, p, d, p]),
+                "or_pagerank_sparse": (i, [i, l, p, p, d, i, p, i, d, p, p, p]),
                 "or_round_bf16": (d, [d]),
                 "or_round_e4m3": (d, [d]),
                 "or_fp8_row_exponent": (i, [p, l]),
@@ -224,6 +225,22 @@ def pagerank(op, n: int, indptr, indices, w0, iters: int, alpha: float = 0.85,
     if G is None:
         G = google_matrix(n, indptr, indices, alpha)
     return mapi(op, G, w0, iters, tol=tol, final_l2=True)
+
+
+def pagerank_sparse(op, n: int, indptr, indices, w0, iters: int, alpha: float = 0.85,
+                    tol: float = 0.0, round32: bool = True):
+    """MAPI-PageRank (§3.3) on the Google matrix of Eq. (11) without forming
+    it; with round32 the entry values are those of an FP32 copy of G.
+    Returns (status, w, iters_done, last_delta)."""
+    ip = np.ascontiguousarray(np.asarray(indptr, dtype=np.int32))
+    ix = np.ascontiguousarray(np.asarray(indices, dtype=np.int32))
+    w0 = _f64(w0)
+    w = np.empty(n)
+    it, dl = C.c_int(0), C.c_double(0.0)
+    st = _get().or_pagerank_sparse(_op(op), n, _ptr(ip), _ptr(ix), float(alpha),
+                                   1 if round32 else 0, _ptr(w0), int(iters), float(tol),
+                                   _ptr(w), C.byref(it), C.byref(dl))
+    return st, w, it.value, dl.value
 
 
 def round_bf16(x) -> np.ndarray:

@@ -356,6 +356,101 @@ void or_google_matrix(long n, const int* indptr, const int* indices,
   for (long i = 0; i < n * n; ++i) G[i] = alpha * G[i] + tele;
 }
 
+/*
+ * MAPI-PageRank on the Google matrix of Eq. (11) without forming it (§3.3).
+ * Every entry of column j is one of a few values: the teleport value
+ * tele = alpha * 0 + (1 - alpha)/n where j has no link to i, alpha * acc + tele
+ * where j links to i (acc = 1/d_j added once per link, as or_google_matrix
+ * adds it), and alpha * (1/n) + tele in a dangling column.  So row i of
+ * G (+) w is the same base sum S = sum_j term(b_j, w_j) for every row (b_j:
+ * the teleport value, or the dangling value), plus, over the in-links of i,
+ * term(g_ij, w_j) - term(tele, w_j).  Exact algebra, not an approximation: the
+ * dense oracle (or_google_matrix, or_mapi) pins it.  With round32 != 0 every
+ * entry value is first rounded to FP32, the values an FP32 copy of G holds.
+ * Steps, stop rule and final l2 step as or_mapi with OR_FINAL_L2.
+ */
+static double pr_value(double v, int round32) { return round32 ? (double)(float)v : v; }
+
+static int cmp_int(const void* a, const void* b) {
+  const int x = *(const int*)a, y = *(const int*)b;
+  return (x > y) - (x < y);
+}
+
+int or_pagerank_sparse(int op, long n, const int* indptr, const int* indices,
+                       double alpha, int round32, const double* w0, int max_iters,
+                       double tol, double* w_out, int* iters_done, double* last_delta) {
+  if (n <= 0 || max_iters < 0) return OR_EINVAL;
+  const double tele = (1.0 - alpha) / (double)n;
+  const double g0 = pr_value(alpha * 0.0 + tele, round32);
+  const double gd = pr_value(alpha * (1.0 / (double)n) + tele, round32);
+  /* per column: its distinct targets and their entry values */
+  long nnz = indptr[n];
+  int* tgt = (int*)malloc(sizeof(int) * (nnz > 0 ? nnz : 1));
+  double* val = (double*)malloc(sizeof(double) * (nnz > 0 ? nnz : 1));
+  long* cnt = (long*)malloc(sizeof(long) * (n + 1));
+  double* w = (double*)malloc(sizeof(double) * n);
+  double* y = (double*)malloc(sizeof(double) * n);
+  long k = 0;
+  for (long j = 0; j < n; ++j) {
+    long b = indptr[j], e = indptr[j + 1], d = e - b;
+    int* t = (int*)malloc(sizeof(int) * (d > 0 ? d : 1));
+    for (long q = 0; q < d; ++q) t[q] = indices[b + q];
+    qsort(t, (size_t)d, sizeof(int), cmp_int);
+    cnt[j] = k;
+    for (long q = 0; q < d;) {
+      long r = q;
+      double acc = 0.0;
+      while (r < d && t[r] == t[q]) { acc += 1.0 / (double)d; ++r; }
+      tgt[k] = t[q];
+      val[k] = pr_value(alpha * acc + tele, round32);
+      ++k;
+      q = r;
+    }
+    free(t);
+  }
+  cnt[n] = k;
+  int status = OR_OK, t = 0;
+  double delta = NAN;
+  for (long i = 0; i < n; ++i) w[i] = w0[i];
+  {
+    double s = or_norm2(w, n);
+    if (s == 0.0) status = OR_EZERONORM;
+    else for (long i = 0; i < n; ++i) w[i] = w[i] / s;
+  }
+  while (status == OR_OK && t < max_iters) {
+    double S = 0.0;
+    for (long j = 0; j < n; ++j)
+      S += or_term(op, (indptr[j + 1] == indptr[j]) ? gd : g0, w[j]);
+    for (long i = 0; i < n; ++i) y[i] = S;
+    for (long j = 0; j < n; ++j) {
+      if (indptr[j + 1] == indptr[j]) continue;
+      for (long q = cnt[j]; q < cnt[j + 1]; ++q)
+        y[tgt[q]] += or_term(op, val[q], w[j]) - or_term(op, g0, w[j]);
+    }
+    double s = (op == OP_DOT) ? or_norm2(y, n) : or_norm1(y, n);
+    if (!isfinite(s)) { status = OR_ENONFINITE; break; }
+    if (s == 0.0) { status = OR_EZERONORM; break; }
+    delta = 0.0;
+    for (long i = 0; i < n; ++i) {
+      double v = y[i] / s;
+      delta += fabs(v - w[i]);
+      w[i] = v;
+    }
+    ++t;
+    if (tol > 0.0 && delta < tol) break;
+  }
+  if (status == OR_OK) {
+    double s = or_norm2(w, n);
+    if (s == 0.0) status = OR_EZERONORM;
+    else for (long i = 0; i < n; ++i) w[i] = w[i] / s;
+  }
+  for (long i = 0; i < n; ++i) w_out[i] = w[i];
+  if (iters_done) *iters_done = t;
+  if (last_delta) *last_delta = delta;
+  free(tgt); free(val); free(cnt); free(w); free(y);
+  return status;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Storage formats.  The paper fixes no storage; these follow the format    */
 /* definitions (IEEE-754 round-to-nearest-even) so that the oracle can run  */

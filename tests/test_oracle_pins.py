@@ -503,3 +503,45 @@ def test_integer_mapi_approximates_float_mapi():
     x0 = np.rint(w0.astype(np.float64) * 2.0 ** q)
     st2, wf, _, _ = oracle.mapi("min1", Aq / 2.0 ** q, x0 / np.abs(x0).sum(), 5, raw_start=True)
     np.testing.assert_allclose(wq / 2.0 ** q, wf, atol=24 * 2.0 ** -q)
+
+
+def _graph_with_duplicates(n, seed):
+    """Out-link CSR with repeated links, dangling nodes and self-links."""
+    r = datagen.rng(seed)
+    ip, ix = [0], []
+    for j in range(n):
+        d = 0 if j % 5 == 0 else int(r.integers(1, 7))
+        ix.extend(int(v) for v in r.integers(0, n, size=d))
+        if d and j % 3 == 0:
+            ix.append(ix[-1])            # a repeated link j -> i
+        ip.append(len(ix))
+    return np.asarray(ip, np.int32), np.asarray(ix, np.int32)
+
+
+@pytest.mark.parametrize("op", ["min1", "min2", "dot"])
+@pytest.mark.parametrize("round32", [False, True])
+def test_sparse_pagerank_equals_dense_definition(op, round32):
+    """The O(E + n) form of G (+) w is the Eq. (11) matrix product: same
+    iterates as Alg. 1 on the dense G (FP64, or G's FP32 values), up to the
+    order of FP64 additions."""
+    for n, seed in ((1, 30), (7, 31), (60, 32), (400, 33)):
+        ip, ix = _graph_with_duplicates(n, seed)
+        G = oracle.google_matrix(n, ip, ix, 0.85)
+        if round32:
+            G = G.astype(np.float32).astype(np.float64)
+        w0 = datagen.start_vector(n, seed=seed, low=0.0, high=1.0).astype(np.float64)
+        st, want, it, dl = oracle.mapi(op, G, w0, 15, final_l2=True)
+        st2, got, it2, dl2 = oracle.pagerank_sparse(op, n, ip, ix, w0, 15, round32=round32)
+        assert (st, it) == (st2, it2)
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+        assert abs(dl - dl2) <= 1e-12
+
+
+def test_sparse_pagerank_stop_rule():
+    ip, ix = datagen.barabasi_albert_digraph(200, m=4, seed=34)
+    w0 = datagen.start_vector(200, seed=34, low=0.0, high=1.0)
+    G = oracle.google_matrix(200, ip, ix, 0.85).astype(np.float32).astype(np.float64)
+    st, want, it, dl = oracle.mapi("min1", G, w0, 500, tol=1e-9, final_l2=True)
+    st2, got, it2, dl2 = oracle.pagerank_sparse("min1", 200, ip, ix, w0, 500, tol=1e-9)
+    assert st == st2 == oracle.OK and it == it2 < 500 and dl2 < 1e-9
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
