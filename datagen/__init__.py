@@ -36,6 +36,7 @@ __all__ = [
     "wishart_instance",
     "small_grid_matrix",
     "wishart_instance_device",
+    "barabasi_albert_digraph_fast",
 ]
 
 DEFAULT_SPIKES = (50.0, 30.0, 20.0, 10.0, 5.0, 4.0, 3.0, 2.0)
@@ -168,3 +169,39 @@ def wishart_instance_device(n: int, seed: int, device="cuda"):
     k = max(1, n // 2)
     w = torch.randn(n, k, generator=g, device=device, dtype=torch.float32)
     return (w @ w.T) / k
+
+
+def barabasi_albert_digraph_fast(n: int, m: int = 8, seed: int = 0):
+    """The preferential-attachment digraph of ``barabasi_albert_digraph``,
+    drawn in blocks for large n: the nodes of a block pick their m distinct
+    targets among the nodes before the block, weighted as in the urn at the
+    block's start (the block grows with the graph, 1/16 of the nodes so far).
+    Same out-link CSR (int32, targets ascending); a different (faster) draw."""
+    r = rng(seed)
+    m = min(m, max(n - 1, 1))
+    urn = np.arange(min(m, n), dtype=np.int64)
+    targets = np.zeros((max(n - m, 0), m), dtype=np.int64)
+    v0 = m
+    while v0 < n:
+        v1 = min(n, v0 + max(64, v0 // 16))
+        cnt = v1 - v0
+        pick = urn[r.integers(0, urn.size, size=(cnt, m))]
+        while True:
+            srt = np.sort(pick, axis=1)
+            dup_rows = np.nonzero((srt[:, 1:] == srt[:, :-1]).any(axis=1))[0]
+            if dup_rows.size == 0:
+                break
+            for k in dup_rows:
+                row = pick[k]
+                _, first = np.unique(row, return_index=True)
+                mask = np.ones(m, dtype=bool)
+                mask[first] = False
+                row[mask] = urn[r.integers(0, urn.size, size=int(mask.sum()))]
+        pick.sort(axis=1)
+        targets[v0 - m:v1 - m] = pick
+        own = np.repeat(np.arange(v0, v1, dtype=np.int64), m + 1)
+        urn = np.concatenate([urn, pick.ravel(), own])
+        v0 = v1
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    indptr[m + 1:] = np.arange(1, n - m + 1, dtype=np.int64) * m
+    return indptr.astype(np.int32), targets.ravel().astype(np.int32)

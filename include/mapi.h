@@ -249,6 +249,28 @@ mapi_status mapi_pagerank(mapi_ctx* ctx, const int* indptr, const int* indices,
                           double tol_l1, float* rank_out, int* iters_done,
                           double* last_delta);
 
+/*
+ * MAPI-PageRank (§3.3) without forming G: each step costs O(E + n) instead
+ * of O(n^2).  Every entry of G (Eq. (11)) is one of three values: the
+ * teleport value (1 - alpha)/n, that value plus alpha * (#links j -> i)/d_j
+ * on a link, or alpha/n plus it in a dangling column, each formed in FP64
+ * and rounded to FP32 exactly as mapi_google_matrix stores them.  Row i of
+ * G (+) w is then one base sum over all columns plus a correction for each
+ * in-link of i.  Same iteration, stop rule and final l2 step as
+ * mapi_pagerank; only the FP32 summation order differs.
+ *   indptr, indices: device out-link CSR (n + 1 and indptr[n] int32; indices
+ *     may be NULL when indptr[n] = 0), checked on the device: an entry out of
+ *     range returns MAPI_EINVAL.
+ *   op: MIN1, MIN2 or DOT.  w0: device n FP32.  rank_out: device n FP32.
+ *   iters_done / last_delta: host scalars (may be NULL).
+ * Errors: MAPI_EINVAL, MAPI_ENOTSUP (a node with more than 16384 in-links),
+ * MAPI_ENOMEM, MAPI_EZERONORM, MAPI_ENONFINITE, MAPI_ECUDA.  Synchronous.
+ */
+mapi_status mapi_pagerank_sparse(mapi_ctx* ctx, const int* indptr, const int* indices, int n,
+                                 double alpha, mapi_op op, const float* w0, int max_iters,
+                                 double tol_l1, float* rank_out, int* iters_done,
+                                 double* last_delta);
+
 
 /* ------------------------------------------------------------------ */
 /* Diagnostics: kernel timing and launch counting.  Not part of the    */

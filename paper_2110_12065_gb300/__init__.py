@@ -24,7 +24,8 @@ __all__ = [
     "mapi_matrix_info", "mapi_matrix_download", "mapi_iterate", "mapi_mincov",
     "mapi_pca_topk", "mapi_google_matrix", "mapi_pagerank", "mapi_profile",
     "mapi_get_stats", "mapi_iterate_noalloc", "mapi_iterate_batched",
-    "mapi_autotune_batched", "mapi_submit", "mapi_poll", "mapi_cancel", "KERNEL_CLASSES",
+    "mapi_autotune_batched", "mapi_submit", "mapi_poll", "mapi_cancel",
+    "mapi_pagerank_sparse", "KERNEL_CLASSES",
     "OP", "ST", "FLAG_FINAL_L2", "FLAG_RAW_START", "SCALE_AUTO",
     "PCA_MINCOV", "PCA_PAIR", "STATUS",
 ]
@@ -111,6 +112,7 @@ def load(path: str | None = None):
         "mapi_pca_topk": [p_, p_, i, i, i, i, d, d, p_, p_, p_],
         "mapi_google_matrix": [p_, p_, p_, i, d, i, C.POINTER(p_)],
         "mapi_pagerank": [p_, p_, p_, i, d, i, i, p_, i, d, p_, p_, p_],
+        "mapi_pagerank_sparse": [p_, p_, p_, i, d, i, p_, i, d, p_, p_, p_],
         "mapi_profile": [p_, i],
         "mapi_get_stats": [p_, C.POINTER(_Stats), i],
         "mapi_iterate_noalloc": [p_, i, i64, i, p_, i, d, u, p_, p_, p_, p_],
@@ -315,6 +317,25 @@ def mapi_pagerank(ctx, indptr, indices, n: int, w0, max_iters: int,
                              C.byref(dl))
     res = (rank_out, it.value, dl.value)
     _check(r, "mapi_pagerank", ctx, partial=res)
+    return res
+
+
+def mapi_pagerank_sparse(ctx, indptr, indices, n: int, w0, max_iters: int,
+                         alpha: float = 0.85, op="min1", tol_l1: float = 0.0, rank_out=None):
+    """MAPI-PageRank (§3.3) in O(E + n) per step, without forming G.  indptr /
+    indices: torch CUDA int32 out-link CSR.  Returns (rank (n,), iters_done,
+    last_delta)."""
+    torch = _torch()
+    if rank_out is None:
+        rank_out = torch.empty(n, dtype=torch.float32, device="cuda")
+    opi = OP[op] if isinstance(op, str) else int(op)
+    it, dl = C.c_int(), C.c_double()
+    r = load().mapi_pagerank_sparse(ctx, C.c_void_p(_dptr(indptr)), C.c_void_p(_dptr(indices)),
+                                    int(n), float(alpha), opi, C.c_void_p(_dptr(w0)),
+                                    int(max_iters), float(tol_l1), C.c_void_p(_dptr(rank_out)),
+                                    C.byref(it), C.byref(dl))
+    res = (rank_out, it.value, dl.value)
+    _check(r, "mapi_pagerank_sparse", ctx, partial=res)
     return res
 
 
