@@ -402,6 +402,24 @@ def run_variants(M, ctx, torch, dev, X, W0d, peaks):
         out[f"pagerank_n16384_{stg}"] = {"iters_per_s": round(100 / (ms / 1e3), 1),
                                          "gemv_gbs": round(gbs, 1),
                                          "hbm_frac": round(gbs / hbm, 4)}
+    # sparse exact MAPI-PageRank: 2^20 nodes, 8 out-links each, 100 steps
+    n = 1 << 20
+    ip, ix = datagen.barabasi_albert_digraph_fast(n, m=8, seed=0)
+    dip, dix = torch.from_numpy(ip).to(dev), torch.from_numpy(ix).to(dev)
+    w0 = torch.from_numpy(datagen.start_vector(n, seed=0, low=0.0, high=1.0)).to(dev)
+    run = lambda: M.mapi_pagerank_sparse(ctx, dip, dix, n, w0, 100)
+    ms = timed(torch, run, 2)
+    st = instrumented(run)
+    gv = st["gemv"]
+    nnz = int(ip[-1])
+    out["pagerank_sparse_n1M"] = {
+        "n": n, "links": nnz, "ms_per_solve": round(ms, 3),
+        "iters_per_s": round(100 / (ms / 1e3), 1),
+        "row_step_us": round(gv["ms"] / max(1, gv["launches"]) * 1e3, 3),
+        "row_step_gbs": round(gv["bytes"] / (gv["ms"] / 1e3) / 1e9, 1) if gv["ms"] else None,
+        "row_step_hbm_frac": round(gv["bytes"] / (gv["ms"] / 1e3) / 1e9 / hbm, 4)
+        if gv["ms"] else None,
+        "algorithmic_bytes_per_row_step": 16 * nnz + 8 * n}
     out["serve_mixed"] = run_serving(M, torch, dev)
     return out
 
@@ -632,6 +650,13 @@ def run_case(case: str):
         _, its = M.mapi_pca_topk(ctx, mat, 2, mode, "min1", 6, float(N), W0)
         M.mapi_matrix_free(ctx, mat)
         out = f"{case}: 2 components x 6 steps, iters {its}"
+    elif case == "pagerank-sparse":
+        n = 1 << 20
+        ip, ix = datagen.barabasi_albert_digraph_fast(n, m=8, seed=0)
+        w0 = torch.from_numpy(datagen.start_vector(n, seed=0, low=0.0, high=1.0)).cuda()
+        _, it, _ = M.mapi_pagerank_sparse(ctx, torch.from_numpy(ip).cuda(),
+                                          torch.from_numpy(ix).cuda(), n, w0, 6)
+        out = f"{case}: n={n}, {it} steps"
     elif case.startswith("pagerank-"):
         st = case.split("-")[1]
         n = 16384
@@ -673,7 +698,7 @@ def main():
     ap.add_argument("--case", default=None,
                     help="run one short solve of a workload for a profiler and exit: "
                          "pair-f32, pair-bf16, mincov-f32, mincov-bf16, pagerank-f32, "
-                         "pagerank-bf16, pagerank-fp8, pagerank-i16, batched-f32, serve")
+                         "pagerank-bf16, pagerank-fp8, pagerank-i16, pagerank-sparse, batched-f32, serve")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)

@@ -31,6 +31,8 @@ constexpr int kSpThreads = 256;
 constexpr int kSpLong = 32;        // rows with more in-links go to a warp
 constexpr int kSpSortThread = 64;  // rows up to this many in-links sort in one thread
 constexpr int kSpSortMax = 16384;  // longest in-link list sorted in shared memory
+constexpr int kSpBatch = 8;        // in-links of a short row loaded together
+constexpr int kSpHuge = 1024;      // rows with more in-links go to a whole CTA
 
 struct SpCtl {
   unsigned counter_a, counter_b;
@@ -44,8 +46,10 @@ struct SpGraph {
   const int* inptr;   // n + 1
   const int* src;     // in-link sources (-1: merged into the previous entry)
   const float* val;   // entry values g_ij
-  const int* longrows;
+  const int* longrows;  // rows with kSpLong < in-links <= kSpHuge, ascending
   int nlong;
+  const int* hugerows;  // rows with more than kSpHuge in-links, ascending
+  int nhuge;
   float g0, gd;
 };
 
@@ -72,29 +76,73 @@ __global__ void k_sp_count(const int* __restrict__ indptr, const int* __restrict
   }
 }
 
-// Exclusive scan of n counts into inptr (n + 1 entries), one CTA.
-__global__ void __launch_bounds__(1024) k_sp_scan(const int* __restrict__ cnt, int n,
-                                                  int* __restrict__ out) {
+// Exclusive scan of n counts into out (n + 1 entries), in three passes: the
+// sum of each CTA's contiguous chunk; one CTA scans those sums; each CTA
+// scans its chunk in tiles of kSpThreads from its offset.
+__global__ void __launch_bounds__(kSpThreads) k_scan_sums(const int* __restrict__ cnt, int n,
+                                                         int chunk, long long* __restrict__ bsum) {
+  __shared__ long long sh[kSpThreads / 32];
+  const long long b = (long long)blockIdx.x * chunk;
+  const long long e = std::min<long long>(n, b + chunk);
+  long long s = 0;
+  for (long long i = b + threadIdx.x; i < e; i += kSpThreads) s += cnt[i];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int q = 0; q < kSpThreads / 32; ++q) t += sh[q];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_blocks(long long* __restrict__ bsum, int nb) {
   __shared__ long long part[1024];
   const int t = threadIdx.x;
-  const long long per = ((long long)n + 1023) / 1024;
-  const long long b = t * per, e = std::min<long long>(n, b + per);
-  long long s = 0;
-  for (long long i = b; i < e; ++i) s += cnt[i];
-  part[t] = s;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const long long v = t >= o ? part[t - o] : 0;
+  long long carry = 0;
+  for (int base = 0; base < nb; base += 1024) {
+    const long long v = base + t < nb ? bsum[base + t] : 0;
+    part[t] = v;
     __syncthreads();
-    part[t] += v;
+    for (int o = 1; o < 1024; o <<= 1) {
+      const long long u = t >= o ? part[t - o] : 0;
+      __syncthreads();
+      part[t] += u;
+      __syncthreads();
+    }
+    if (base + t < nb) bsum[base + t] = carry + part[t] - v;  // exclusive
+    const long long tot = part[1023];
     __syncthreads();
+    carry += tot;
   }
-  long long run = part[t] - s;
-  for (long long i = b; i < e; ++i) {
-    out[i] = (int)run;
-    run += cnt[i];
+}
+
+__global__ void __launch_bounds__(kSpThreads) k_scan_final(const int* __restrict__ cnt, int n,
+                                                          int chunk,
+                                                          const long long* __restrict__ bsum,
+                                                          int* __restrict__ out) {
+  __shared__ long long part[kSpThreads];
+  const long long b = (long long)blockIdx.x * chunk;
+  const long long e = std::min<long long>(n, b + chunk);
+  long long carry = bsum[blockIdx.x];
+  const int t = threadIdx.x;
+  for (long long base = b; base < e; base += kSpThreads) {
+    const long long v = base + t < e ? cnt[base + t] : 0;
+    part[t] = v;
+    __syncthreads();
+    for (int o = 1; o < kSpThreads; o <<= 1) {
+      const long long u = t >= o ? part[t - o] : 0;
+      __syncthreads();
+      part[t] += u;
+      __syncthreads();
+    }
+    if (base + t < e) out[base + t] = (int)(carry + part[t] - v);
+    const long long tot = part[kSpThreads - 1];
+    __syncthreads();
+    carry += tot;
   }
-  if (t == 1023) out[n] = (int)part[1023];
+  if (e == n && b < e && t == 0) out[n] = (int)carry;
 }
 
 __global__ void k_sp_fill(const int* __restrict__ indptr, const int* __restrict__ indices, int n,
@@ -132,14 +180,12 @@ __device__ __forceinline__ void sp_merge_run(int* src, float* val, int p, int e,
 // Short lists: one thread each (insertion sort); long ones are queued.
 __global__ void k_sp_sort_short(int n, const int* __restrict__ inptr, int* __restrict__ src,
                                 float* __restrict__ val, const int* __restrict__ deg,
-                                double alpha, double tele, int* __restrict__ sortq,
-                                int* __restrict__ longrows, SpCtl* ctl) {
+                                double alpha, double tele, int* __restrict__ sortq, SpCtl* ctl) {
   if (ctl->bad) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int b = inptr[i], e = inptr[i + 1];
-    if (e - b > kSpLong) longrows[atomicAdd(&sortq[1], 1)] = i;
     if (e - b > kSpSortThread) {
-      sortq[2 + atomicAdd(&sortq[0], 1)] = i;
+      sortq[4 + atomicAdd(&sortq[0], 1)] = i;
       continue;
     }
     for (int p = b + 1; p < e; ++p) {
@@ -156,6 +202,27 @@ __global__ void k_sp_sort_short(int n, const int* __restrict__ inptr, int* __res
   }
 }
 
+// Row classes by in-link count: flags for the two ordered lists.
+__global__ void k_sp_flags(int n, const int* __restrict__ inptr, int* __restrict__ fl,
+                           int* __restrict__ fh) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int d = inptr[i + 1] - inptr[i];
+    fl[i] = (d > kSpLong && d <= kSpHuge) ? 1 : 0;
+    fh[i] = d > kSpHuge ? 1 : 0;
+  }
+}
+
+// The rows of each class in ascending order (positions from the scans).
+__global__ void k_sp_lists(int n, const int* __restrict__ inptr, const int* __restrict__ pl,
+                           const int* __restrict__ ph, int* __restrict__ longrows,
+                           int* __restrict__ hugerows) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int d = inptr[i + 1] - inptr[i];
+    if (d > kSpLong && d <= kSpHuge) longrows[pl[i]] = i;
+    if (d > kSpHuge) hugerows[ph[i]] = i;
+  }
+}
+
 // Long lists: one CTA each, bitonic sort in shared memory.
 __global__ void __launch_bounds__(1024) k_sp_sort_long(const int* __restrict__ inptr,
                                                        int* __restrict__ src,
@@ -166,7 +233,7 @@ __global__ void __launch_bounds__(1024) k_sp_sort_long(const int* __restrict__ i
   extern __shared__ int key[];
   const int nq = sortq[0];
   for (int r = blockIdx.x; r < nq; r += gridDim.x) {
-    const int i = sortq[2 + r];
+    const int i = sortq[4 + r];
     const int b = inptr[i], e = inptr[i + 1], len = e - b;
     if (len > kSpSortMax) {
       if (threadIdx.x == 0) ctl->bad = 2;
@@ -276,30 +343,56 @@ __global__ void __launch_bounds__(kSpThreads)
     const int b = g.inptr[i], e = g.inptr[i + 1];
     if (e - b > kSpLong) continue;
     float c = 0.f;
-    for (int q = b; q < e; ++q) {
-      const int j = g.src[q];
-      if (j < 0) continue;
-      const float2 v = wt[j];
-      c += Op<OP>::term(g.val[q], Op<OP>::prep(v.x), 0.f) - v.y;
+    // kSpBatch in-links at a time: their sources and values, then their
+    // gathers, all in flight before any is used (the order of the sum is
+    // the in-link order)
+    for (int q0 = b; q0 < e; q0 += kSpBatch) {
+      int jv[kSpBatch];
+      float gv[kSpBatch];
+#pragma unroll
+      for (int k = 0; k < kSpBatch; ++k) {
+        jv[k] = q0 + k < e ? __ldg(&g.src[q0 + k]) : -1;
+        gv[k] = q0 + k < e ? __ldg(&g.val[q0 + k]) : 0.f;
+      }
+      float2 wv[kSpBatch];
+#pragma unroll
+      for (int k = 0; k < kSpBatch; ++k) wv[k] = jv[k] >= 0 ? wt[jv[k]] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < kSpBatch; ++k)
+        if (jv[k] >= 0) c += Op<OP>::term(gv[k], Op<OP>::prep(wv[k].x), 0.f) - wv[k].y;
     }
     const float yi = S + c;
     y[i] = yi;
     kn.add(norm_l2 ? yi * yi : fabsf(yi));
   }
-  // long rows: one warp each, lanes over the sources, fixed butterfly
-  const int lane = threadIdx.x & 31;
+  // long rows: one warp each, lanes over the sources (four per lane in
+  // flight), fixed butterfly
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto lane_sum = [&](int b, int e, int first, int stride) {
+    float c = 0.f;
+    for (int q0 = b + first; q0 < e; q0 += 4 * stride) {
+      int jv[4];
+      float gv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int q = q0 + k * stride;
+        jv[k] = q < e ? __ldg(&g.src[q]) : -1;
+        gv[k] = q < e ? __ldg(&g.val[q]) : 0.f;
+      }
+      float2 wv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) wv[k] = jv[k] >= 0 ? wt[jv[k]] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (jv[k] >= 0) c += Op<OP>::term(gv[k], Op<OP>::prep(wv[k].x), 0.f) - wv[k].y;
+    }
+    return c;
+  };
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int r = gw; r < g.nlong; r += nw) {
     const int i = g.longrows[r];
-    const int b = g.inptr[i], e = g.inptr[i + 1];
-    float c = 0.f;
-    for (int q = b + lane; q < e; q += 32) {
-      const int j = g.src[q];
-      if (j < 0) continue;
-      const float2 v = wt[j];
-      c += Op<OP>::term(g.val[q], Op<OP>::prep(v.x), 0.f) - v.y;
-    }
+    float c = lane_sum(g.inptr[i], g.inptr[i + 1], lane, 32);
 #pragma unroll
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     const float yi = S + c;
@@ -307,6 +400,26 @@ __global__ void __launch_bounds__(kSpThreads)
       y[i] = yi;
       kn.add(norm_l2 ? yi * yi : fabsf(yi));
     }
+  }
+  // huge rows: one CTA each, threads over the sources, warp then CTA sums in
+  // a fixed order
+  __shared__ float hw[kSpThreads / 32];
+  for (int r = blockIdx.x; r < g.nhuge; r += gridDim.x) {
+    const int i = g.hugerows[r];
+    float c = lane_sum(g.inptr[i], g.inptr[i + 1], threadIdx.x, kSpThreads);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) hw[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+#pragma unroll
+      for (int q = 0; q < kSpThreads / 32; ++q) t += hw[q];
+      const float yi = S + t;
+      y[i] = yi;
+      kn.add(norm_l2 ? yi * yi : fabsf(yi));
+    }
+    __syncthreads();
   }
   const float pn = block_sum<kSpThreads>(kn.value(), sh);
   if (threadIdx.x == 0) part[blockIdx.x] = pn;
@@ -367,6 +480,21 @@ __global__ void __launch_bounds__(1024) k_sp_norm2(const float* __restrict__ w, 
   if (threadIdx.x == 0) ctl->s2 = s;
 }
 
+// out[0 .. n] = exclusive scan of cnt[0 .. n), out[n] the total.
+mapi_status sp_scan(mapi_ctx* ctx, cudaStream_t s, const int* cnt, int n, int* out,
+                    long long* bsum, int nb) {
+  const int chunk = (n + nb - 1) / nb;
+  const int used = (n + chunk - 1) / chunk;
+  k_scan_sums<<<used, kSpThreads, 0, s>>>(cnt, n, chunk, bsum);
+  MAPI_CUDA_TRY(ctx, cudaGetLastError());
+  k_scan_blocks<<<1, 1024, 0, s>>>(bsum, used);
+  MAPI_CUDA_TRY(ctx, cudaGetLastError());
+  k_scan_final<<<used, kSpThreads, 0, s>>>(cnt, n, chunk, bsum, out);
+  MAPI_CUDA_TRY(ctx, cudaGetLastError());
+  count_launch(ctx, 3);
+  return MAPI_OK;
+}
+
 template <int OP>
 mapi_status sp_solve(mapi_ctx* ctx, cudaStream_t s, const SpGraph& g, float* wb0, float* wb1,
                      float* y, float2* wt, float* part, SpCtl* ctl, int grid, int max_iters,
@@ -423,13 +551,14 @@ extern "C" mapi_status mapi_pagerank_sparse(mapi_ctx* ctx, const int* indptr, co
   if (nnz > 0 && !indices) return fail(ctx, MAPI_EINVAL, "null indices");
   const int grid = std::max(1, std::min((n + kSpThreads - 1) / kSpThreads, 8 * ctx->sm_count));
   // one device block: ctl | deg | incount | inptr | fill | sortq | longrows |
-  // src | val | wb0 | wb1 | y | wt | part
+  // hugerows | pos_long | pos_huge | src | val | wb0 | wb1 | y | wt | part
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t E = (size_t)std::max(nnz, 1), N = (size_t)n;
-  const size_t sizes[] = {al(sizeof(SpCtl)), al(4 * N),     al(4 * N),      al(4 * (N + 1)),
-                          al(4 * N),         al(4 * (N + 2)), al(4 * N),     al(4 * E),
-                          al(4 * E),         al(4 * N),     al(4 * N),      al(4 * N),
-                          al(8 * N),         al(4 * 3 * (size_t)grid)};
+  const size_t sizes[] = {al(sizeof(SpCtl)), al(4 * N),       al(4 * N),       al(4 * (N + 1)),
+                          al(4 * N),         al(4 * (N + 4)), al(4 * N),       al(4 * N),
+                          al(4 * (N + 1)),   al(4 * (N + 1)), al(4 * E),       al(4 * E),
+                          al(4 * N),         al(4 * N),       al(4 * N),       al(8 * N),
+                          al(4 * 3 * (size_t)grid),     al(8 * (size_t)grid)};
   size_t total = 0;
   for (size_t b : sizes) total += b;
   char* base = nullptr;
@@ -450,25 +579,37 @@ extern "C" mapi_status mapi_pagerank_sparse(mapi_ctx* ctx, const int* indptr, co
   int* fill = (int*)take(4);
   int* sortq = (int*)take(5);
   int* longrows = (int*)take(6);
-  int* src = (int*)take(7);
-  float* val = (float*)take(8);
-  float* wb0 = (float*)take(9);
-  float* wb1 = (float*)take(10);
-  float* y = (float*)take(11);
-  float2* wt = (float2*)take(12);
-  float* part = (float*)take(13);
+  int* hugerows = (int*)take(7);
+  int* pos_long = (int*)take(8);
+  int* pos_huge = (int*)take(9);
+  int* src = (int*)take(10);
+  float* val = (float*)take(11);
+  float* wb0 = (float*)take(12);
+  float* wb1 = (float*)take(13);
+  float* y = (float*)take(14);
+  float2* wt = (float2*)take(15);
+  float* part = (float*)take(16);
+  long long* bsum = (long long*)take(17);
   mapi_status st = MAPI_OK;
   auto run = [&]() -> mapi_status {
-    MAPI_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, (char*)src - base, s));  // ctl .. longrows
+    MAPI_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, (char*)longrows - base, s));  // ctl .. sortq
     k_sp_count<<<grid, kSpThreads, 0, s>>>(indptr, indices, n, nnz, deg, incount, ctl);
     MAPI_CUDA_TRY(ctx, cudaGetLastError());
-    k_sp_scan<<<1, 1024, 0, s>>>(incount, n, inptr);
-    MAPI_CUDA_TRY(ctx, cudaGetLastError());
+    mapi_status r0 = sp_scan(ctx, s, incount, n, inptr, bsum, grid);
+    if (r0 != MAPI_OK) return r0;
     k_sp_fill<<<grid, kSpThreads, 0, s>>>(indptr, indices, n, inptr, fill, src, ctl);
     MAPI_CUDA_TRY(ctx, cudaGetLastError());
     const double tele = (1.0 - alpha) / (double)n;
     k_sp_sort_short<<<grid, kSpThreads, 0, s>>>(n, inptr, src, val, deg, alpha, tele, sortq,
-                                                longrows, ctl);
+                                                ctl);
+    MAPI_CUDA_TRY(ctx, cudaGetLastError());
+    // ordered lists of the long and huge rows (flags in the spent count and
+    // fill arrays, positions by scan)
+    k_sp_flags<<<grid, kSpThreads, 0, s>>>(n, inptr, incount, fill);
+    MAPI_CUDA_TRY(ctx, cudaGetLastError());
+    if ((r0 = sp_scan(ctx, s, incount, n, pos_long, bsum, grid)) != MAPI_OK) return r0;
+    if ((r0 = sp_scan(ctx, s, fill, n, pos_huge, bsum, grid)) != MAPI_OK) return r0;
+    k_sp_lists<<<grid, kSpThreads, 0, s>>>(n, inptr, pos_long, pos_huge, longrows, hugerows);
     MAPI_CUDA_TRY(ctx, cudaGetLastError());
     const size_t lsm = sizeof(int) * kSpSortMax;
     MAPI_CUDA_TRY(ctx, cudaFuncSetAttribute((const void*)k_sp_sort_long,
@@ -477,10 +618,11 @@ extern "C" mapi_status mapi_pagerank_sparse(mapi_ctx* ctx, const int* indptr, co
     k_sp_sort_long<<<ctx->sm_count, 1024, lsm, s>>>(inptr, src, val, deg, alpha, tele, sortq,
                                                    ctl);
     MAPI_CUDA_TRY(ctx, cudaGetLastError());
-    count_launch(ctx, 5);
+    count_launch(ctx, 9);
     int hq[2] = {0, 0};
     SpCtl hc;
-    MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(hq, sortq, sizeof(hq), cudaMemcpyDeviceToHost, s));
+    MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(&hq[0], pos_long + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(&hq[1], pos_huge + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, s));
     MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (hc.bad == 1) return fail(ctx, MAPI_EINVAL, "indptr or indices out of range");
@@ -492,7 +634,9 @@ extern "C" mapi_status mapi_pagerank_sparse(mapi_ctx* ctx, const int* indptr, co
     g.src = src;
     g.val = val;
     g.longrows = longrows;
-    g.nlong = hq[1];
+    g.nlong = hq[0];
+    g.hugerows = hugerows;
+    g.nhuge = hq[1];
     g.g0 = (float)(alpha * 0.0 + tele);
     g.gd = (float)(alpha * (1.0 / (double)n) + tele);
     k_sp_start<<<1, 1024, 0, s>>>(w0, n, wb0, ctl);
