@@ -380,7 +380,7 @@ struct PairArgs {
 // rows), yfull and cbuf (D_pad each), four scan buffers and the component's
 // w, sorted c, perm and ub (kDeflMaxD each).
 // one padded array of the deflation: kDeflMaxD entries, one spare word per 32
-constexpr int kDeflPadded = kDeflMaxD + kDeflMaxD / 32;
+constexpr int kDeflPadded = kDeflMaxD + kDeflMaxD / 8;
 __host__ __device__ constexpr int pair_epi_floats(int rc, int d_pad) {
   return 3 * rc + 3 * d_pad + 2 * 8 * kDeflPadded;
 }
@@ -388,9 +388,14 @@ __host__ __device__ constexpr int pair_epi_floats(int rc, int d_pad) {
 constexpr int kPairMaxClusters = 80;  // partials per row the epilogue reads at once
 constexpr int kEpiHalf = kPairWarps * 32 / 2;  // threads that load one component
 
-// Index of sorted position p in a padded deflation array: lane l's run of
-// 32 positions [32 l, 32 l + 32) then falls on 32 different banks.
-__device__ __forceinline__ int dpad(int p) { return p + (p >> 5); }
+// Index of sorted position p in a padded deflation array: the 32 lanes' runs
+// of 8 positions [8 l, 8 l + 8) then fall on 32 different banks.
+__device__ __forceinline__ int dpad(int p) { return p + (p >> 3); }
+
+// Barrier of the 4 warps that deflate one component (named barriers 1, 2).
+__device__ __forceinline__ void group_bar(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(128) : "memory");
+}
 
 // Epilogue of one pair step, run by the last cluster to finish: CTA r owns
 // rows [r*RS, (r+1)*RS) (the rows it streamed).  y = sum of the cluster
@@ -446,10 +451,10 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
     wo[i] = d < D ? a.w[d] : 0.f;
     const float4* src = reinterpret_cast<const float4*>(a.ypart + (int64_t)d * a.pstride);
     const int p4 = a.pstride / 4;
-    constexpr int B4 = kPairMaxClusters / 8;  // two batches of loads in flight
+    constexpr int B4 = kPairMaxClusters / 4;  // every partial in flight at once
     float sum = 0.f;
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 1; ++b) {
       float4 v[B4];
 #pragma unroll
       for (int g = 0; g < B4; ++g)
@@ -476,9 +481,14 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
       cbuf[a.D_pad + i] = 0.f;
     }
     __syncthreads();
-    if (warp < 2) {
-      float* cb = cbuf + warp * a.D_pad;
-      float* sA = arrays(warp);
+    {
+      // group g = warps 4g .. 4g + 3 deflates component r + CS g (and every
+      // 2 CS-th after it); warp wq of the group scans sorted positions
+      // [256 wq, 256 wq + 256), eight per lane
+      const int g = warp >> 2, wq = warp & 3, tg = threadIdx.x & 127;
+      __shared__ float gtot[2][4][4];
+      float* cb = cbuf + g * a.D_pad;
+      float* sA = arrays(g);
       float* sB = sA + kDeflPadded;
       float* sA2 = sB + kDeflPadded;
       float* sB2 = sA2 + kDeflPadded;
@@ -487,25 +497,30 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
       const int* perm_s = reinterpret_cast<const int*>(cs_s + kDeflPadded);
       const int* ub_s = perm_s + kDeflPadded;
       const bool two = a.defl.op == MAPI_OP_MIN2;
-      for (int m = r + CS * warp; m < a.defl.nprev; m += 2 * CS) {
-        if (m >= 2 * CS) {  // more components than deflating warps
-          __syncwarp();
-          load_comp(m, warp, lane, 32);
+      for (int m = r + CS * g; m < a.defl.nprev; m += 2 * CS) {
+        if (m >= 2 * CS) {  // more components than groups
+          group_bar(g);
+          load_comp(m, g, tg, 128);
         }
-        __syncwarp();
+        group_bar(g);
         if (dot) {
           float pd = 0.f;
-          for (int i = lane; i < D; i += 32) pd += wm_s[i] * yfull[i];
+          for (int i = tg; i < D; i += 128) pd += wm_s[i] * yfull[i];
 #pragma unroll
           for (int o = 16; o; o >>= 1) pd += __shfl_xor_sync(0xffffffffu, pd, o);
-          for (int i = lane; i < D; i += 32) cb[i] += wm_s[i] * pd;
+          if (lane == 0) gtot[g][wq][0] = pd;
+          group_bar(g);
+          const float dv = gtot[g][0][0] + gtot[g][1][0] + gtot[g][2][0] + gtot[g][3][0];
+          for (int i = tg; i < D; i += 128) cb[i] += wm_s[i] * dv;
+          group_bar(g);
           continue;
         }
-        // lane l scans the sorted positions [32 l, 32 l + 32)
+        // running sums over this lane's 8 positions
         float ra = 0.f, rb = 0.f, ra2 = 0.f, rb2 = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-          const int p = lane * 32 + k;
+        const int p0 = wq * 256 + lane * 8;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int p = p0 + k;
           if (p < D) {
             const int i = perm_s[dpad(p)];
             const float y = yfull[i];
@@ -513,17 +528,19 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
             const float z = sgnf(wm_s[i]) * y;
             ra += c * z;
             rb += z;
-            sA[dpad(p)] = ra;
-            sB[dpad(p)] = rb;
             if (two) {
               ra2 += c * y;
               rb2 += y;
-              sA2[dpad(p)] = ra2;
-              sB2[dpad(p)] = rb2;
             }
           }
+          sA[dpad(p)] = ra;
+          sB[dpad(p)] = rb;
+          if (two) {
+            sA2[dpad(p)] = ra2;
+            sB2[dpad(p)] = rb2;
+          }
         }
-        // exclusive offsets of the lanes' runs
+        // lane offsets within the warp, then warp offsets within the group
         float oa = ra, ob = rb, oa2 = ra2, ob2 = rb2;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -538,26 +555,41 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
             ob2 += nb2;
           }
         }
-        const float totB = __shfl_sync(0xffffffffu, ob, 31);
-        const float totB2 = __shfl_sync(0xffffffffu, ob2, 31);
+        if (lane == 31) {
+          gtot[g][wq][0] = oa;
+          gtot[g][wq][1] = ob;
+          gtot[g][wq][2] = oa2;
+          gtot[g][wq][3] = ob2;
+        }
         oa -= ra;
         ob -= rb;
         oa2 -= ra2;
         ob2 -= rb2;
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-          const int p = lane * 32 + k;
-          if (p < D) {
-            sA[dpad(p)] += oa;
-            sB[dpad(p)] += ob;
-            if (two) {
-              sA2[dpad(p)] += oa2;
-              sB2[dpad(p)] += ob2;
-            }
+        group_bar(g);
+        float totB = 0.f, totB2 = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (q < wq) {
+            oa += gtot[g][q][0];
+            ob += gtot[g][q][1];
+            oa2 += gtot[g][q][2];
+            ob2 += gtot[g][q][3];
+          }
+          totB += gtot[g][q][1];
+          totB2 += gtot[g][q][3];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int p = p0 + k;
+          sA[dpad(p)] += oa;
+          sB[dpad(p)] += ob;
+          if (two) {
+            sA2[dpad(p)] += oa2;
+            sB2[dpad(p)] += ob2;
           }
         }
-        __syncwarp();
-        for (int i = lane; i < D; i += 32) {
+        group_bar(g);
+        for (int i = tg; i < D; i += 128) {
           const float wi = wm_s[i], ci = fabsf(wi);
           const int q = dpad(ub_s[i]);
           float v = sgnf(wi) * (sA[q] + ci * (totB - sB[q]));
@@ -828,17 +860,22 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
   // the next step's kernel may launch now (it waits for this grid to finish
   // before it reads anything this step writes)
   cudaTriggerProgrammaticLaunchCompletion();
-  // last-cluster election: the cluster that finishes last runs the epilogue
+  // last-cluster election: every CTA takes a ticket once its partials are
+  // visible; the cluster holding the last ticket runs the epilogue
   __syncthreads();
-  if (threadIdx.x == 0) __threadfence();
-  cluster.sync();
-  if (crank == 0 && threadIdx.x == 0) {
+  if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned t = atomicAdd(&a.ctl->counter, 1u);
-    const int last = (t == (unsigned)a.nclusters - 1) ? 1 : 0;
-    for (int q = 0; q < kPairCluster; ++q) *cluster.map_shared_rank(&s_last, q) = last;
+    s_last = (t == (unsigned)(a.nclusters * kPairCluster) - 1) ? 1 : 0;
   }
   cluster.sync();
-  if (!s_last) return;
+  int last = 0;
+#pragma unroll
+  for (int q = 0; q < kPairCluster; ++q) last |= *cluster.map_shared_rank(&s_last, q);
+  if (!last) {
+    cluster.sync();  // peers may still read this CTA's ticket until here
+    return;
+  }
   __threadfence();
   pair_epilogue<RC>(a, cluster, reinterpret_cast<float*>(stage));
 }
