@@ -363,8 +363,7 @@ struct PairArgs {
   int nclusters;
   const float* w;  // current iterate (D entries + zero padding)
   float* w_next;   // next iterate (written by the last cluster)
-  float* ypart;    // [D_pad][pstride] partial row sums, one column per cluster
-  int pstride;     // nclusters rounded up to a multiple of 4
+  float* ypart;    // [nclusters][D_pad] partial row sums, one row per cluster
   int D_pad;       // rows covered by one cluster (4 * 8 * RW)
   IterCtl* ctl;
   DeflArgs defl;
@@ -449,25 +448,20 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
   for (int i = threadIdx.x; i < RS; i += NT) {
     const int d = r0 + i;
     wo[i] = d < D ? a.w[d] : 0.f;
-    const float4* src = reinterpret_cast<const float4*>(a.ypart + (int64_t)d * a.pstride);
-    const int p4 = a.pstride / 4;
-    constexpr int B4 = kPairMaxClusters / 4;  // every partial in flight at once
+    // cluster-major partials: a warp's 32 rows of one cluster are 128
+    // contiguous bytes
+    const float* src = a.ypart + d;
+    constexpr int B = kPairMaxClusters / 2;  // two batches of loads in flight
     float sum = 0.f;
 #pragma unroll
-    for (int b = 0; b < 1; ++b) {
-      float4 v[B4];
+    for (int b = 0; b < 2; ++b) {
+      float v[B];
 #pragma unroll
-      for (int g = 0; g < B4; ++g)
-        v[g] = b * B4 + g < p4 ? src[b * B4 + g] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int g = 0; g < B; ++g)
+        v[g] = b * B + g < a.nclusters ? __ldcg(src + (int64_t)(b * B + g) * a.D_pad) : 0.f;
 #pragma unroll
-      for (int g = 0; g < B4; ++g) {
-        if (b * B4 + g < p4) {
-          sum += v[g].x;
-          sum += v[g].y;
-          sum += v[g].z;
-          sum += v[g].w;
-        }
-      }
+      for (int g = 0; g < B; ++g)
+        if (b * B + g < a.nclusters) sum += v[g];
     }
     ys[i] = d < D ? sum / a.denom : 0.f;
   }
@@ -850,7 +844,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
     }
     constexpr int grp = 32 / RW;
     if ((lane & (grp - 1)) == 0)
-      a.ypart[(int64_t)(rbase + lane / grp) * a.pstride + cid] = acc[0];
+      a.ypart[(int64_t)cid * a.D_pad + rbase + lane / grp] = acc[0];
   }
   if (threadIdx.x == 0 && s_err) {
     // a tile or a peer's partials never arrived: report it; the solve stops
@@ -1045,8 +1039,6 @@ static mapi_status plan_pair(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, PairL
   return MAPI_OK;
 }
 
-static int pair_pstride(int nclusters) { return (nclusters + 3) / 4 * 4; }
-
 // Tiles per cluster whose lines are kept in L2 for the next step: together
 // they fill about 60 % of L2 (the rest: stages, partials and the data of
 // other streams).  When that covers all of a cluster's tiles, X stays in L2.
@@ -1071,7 +1063,6 @@ static mapi_status launch_pair_step(mapi_ctx* ctx, cudaStream_t s, const PairLau
   pa.w = w;
   pa.w_next = w_next;
   pa.ypart = ypart;
-  pa.pstride = pair_pstride(pl.clusters);
   pa.D_pad = kPairCluster * kPairWarps * pl.rw;
   pa.ctl = ctl;
   pa.defl = defl;
@@ -1175,10 +1166,7 @@ mapi_status pca_enqueue(mapi_ctx* ctx, cudaStream_t s, const mapi_mat* X, const 
     }
     return MAPI_OK;
   }
-  // pair mode; the padding columns of the partial rows must read as zero
-  MAPI_CUDA_TRY(ctx, cudaMemsetAsync(ctx->ypart.p, 0,
-                                     sizeof(float) * (size_t)pair_pstride(p.pl.clusters) * p.D_pad,
-                                     s));
+  // pair mode
   float* wb0 = (float*)ctx->wbuf0.p;
   float* wb1 = (float*)ctx->wbuf1.p;
   IterCtl* ctl = (IterCtl*)ctx->ctl.p;
@@ -1263,7 +1251,7 @@ mapi_status run_pca(mapi_ctx* ctx, const mapi_mat* X, int k, int mode, mapi_op o
     if ((st = ensure(ctx, ctx->wbuf0, sizeof(float) * p.wst)) != MAPI_OK ||
         (st = ensure(ctx, ctx->wbuf1, sizeof(float) * p.wst)) != MAPI_OK ||
         (st = ensure(ctx, ctx->ypart,
-                     sizeof(float) * (size_t)pair_pstride(p.pl.clusters) * p.D_pad)) != MAPI_OK ||
+                     sizeof(float) * (size_t)p.pl.clusters * p.D_pad)) != MAPI_OK ||
         (st = ensure(ctx, ctx->ctl, sizeof(IterCtl))) != MAPI_OK ||
         (st = ensure(ctx, ctx->pca_defl, sizeof(int) * 3 * (size_t)k * p.D_pad)) != MAPI_OK)
       return st;
