@@ -62,39 +62,61 @@ __device__ __forceinline__ void cta_product(const BatchDev& it, const float* __r
         dst[r].raw = c < it.chunks ? ld_stream(rowp[r] + (int64_t)c * 16) : make_uint4(0, 0, 0, 0);
     };
     auto consume = [&](const Ch (&src)[R], int c) {
+      // every iterate entry of the chunk's columns is read from shared memory
+      // before the first is used, so the reads overlap
+      float wv[E][V];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int j = c * E + e;
-        float wv[V];
         if constexpr (V == 4) {
           const float4 q = *reinterpret_cast<const float4*>(w_s + j * 4);
-          wv[0] = q.x;
-          wv[1] = q.y;
-          wv[2] = q.z;
-          wv[3] = q.w;
+          wv[e][0] = q.x;
+          wv[e][1] = q.y;
+          wv[e][2] = q.z;
+          wv[e][3] = q.w;
         } else {
 #pragma unroll
-          for (int v = 0; v < V; ++v) wv[v] = w_s[j * V + v];
+          for (int v = 0; v < V; ++v) wv[e][v] = w_s[j * V + v];
         }
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          const auto p = Op<OP>::prep(wv[v]);
+          const auto p = Op<OP>::prep(wv[e][v]);
 #pragma unroll
           for (int r = 0; r < R; ++r) acc[r][v] = Op<OP>::term(src[r].get(e), p, acc[r][v]);
         }
       }
     };
-    // software pipeline: the next chunk of every row is in flight while the
-    // current one is consumed
-    Ch b0[R], b1[R];
-    int c = lane;
-    load(b0, c);
-    for (; c < it.chunks; c += 64) {
+    // software pipeline: the next chunks of every row are in flight while
+    // the current one is consumed (two ahead for R <= 4, one for R = 8)
+    if constexpr (R <= 4) {
+      Ch b0[R], b1[R], b2[R];
+      int c = lane;
+      load(b0, c);
       load(b1, c + 32);
-      consume(b0, c);
-      if (c + 32 >= it.chunks) break;
-      load(b0, c + 64);
-      consume(b1, c + 32);
+      for (; c < it.chunks; c += 96) {
+        load(b2, c + 64);
+        consume(b0, c);
+        if (c + 32 >= it.chunks) break;
+        load(b0, c + 96);
+        consume(b1, c + 32);
+        if (c + 64 >= it.chunks) break;
+        load(b1, c + 128);
+        consume(b2, c + 64);
+      }
+    } else {
+      Ch b0[R], b1[R];
+      int c = lane;
+      load(b0, c);
+      for (; c < it.chunks; c += 64) {
+        load(b1, c + 32);
+        consume(b0, c);
+        if (c + 32 >= it.chunks) break;
+        load(b0, c + 64);
+        consume(b1, c + 32);
+      }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
