@@ -56,11 +56,15 @@ struct ServeReq {
 
 struct Server {
   mapi_ctx* parent = nullptr;
-  mapi_ctx* child = nullptr;
-  std::thread th;
+  mapi_ctx* child = nullptr;    // the loop's context: rounds, deflation, copies out
+  mapi_ctx* bchild = nullptr;   // the builder's context: uploads, Eq. (5) / (11)
+  std::thread th, bth;
   std::mutex mu;
-  std::condition_variable cv;
-  bool stop = false;
+  std::condition_variable cv, bcv;
+  bool stop = false, bstop = false;
+  std::deque<ServeReq*> to_build;  // admitted, waiting for the builder
+  std::deque<ServeReq*> built;     // built, waiting for the loop
+  std::vector<mapi_mat*> to_free;  // matrices of finished requests (builder's)
   uint64_t next_ticket = 1;
   std::deque<ServeReq*> queue;
   std::map<uint64_t, ServeReq*> tickets;
@@ -146,10 +150,20 @@ void dev_free(mapi_ctx* c, void* p) {
   if (p) cudaFreeAsync(p, c->stream);
 }
 
-void release(Server* sv, ServeReq* q) {
-  mapi_ctx* c = sv->child;
-  if (q->X) mapi_matrix_free(c, q->X);
-  if (q->G) mapi_matrix_free(c, q->G);
+// Frees a request's device memory from the calling thread's context (the
+// loop's or the builder's).  The packed matrices belong to the builder's
+// context: the loop hands them to the builder to free.
+void release(Server* sv, ServeReq* q, bool in_builder) {
+  mapi_ctx* c = in_builder ? sv->bchild : sv->child;
+  if (in_builder) {
+    if (q->X) mapi_matrix_free(c, q->X);
+    if (q->G) mapi_matrix_free(c, q->G);
+  } else if (q->X || q->G) {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    if (q->X) sv->to_free.push_back(q->X);
+    if (q->G) sv->to_free.push_back(q->G);
+    sv->bcv.notify_all();
+  }
   for (void* p : {(void*)q->C, (void*)q->Cc, (void*)q->Q, (void*)q->P, (void*)q->w0,
                   (void*)q->wb[0], (void*)q->wb[1]})
     dev_free(c, p);
@@ -157,10 +171,10 @@ void release(Server* sv, ServeReq* q) {
   q->C = q->Cc = q->Q = q->P = q->w0 = q->wb[0] = q->wb[1] = nullptr;
 }
 
-// Loop thread: record the outcome and hand the request back to mapi_poll.
-void finish(Server* sv, ServeReq* q, mapi_status s) {
-  release(sv, q);
-  cudaStreamSynchronize(sv->child->stream);
+// Record the outcome and hand the request back to mapi_poll.
+void finish(Server* sv, ServeReq* q, mapi_status s, bool in_builder = false) {
+  release(sv, q, in_builder);
+  cudaStreamSynchronize(in_builder ? sv->bchild->stream : sv->child->stream);
   const Clock::time_point t = Clock::now();
   std::lock_guard<std::mutex> lock(sv->mu);
   q->res.status = s;
@@ -175,9 +189,9 @@ void finish(Server* sv, ServeReq* q, mapi_status s) {
   sv->cv.notify_all();
 }
 
-// Build the request's matrix and vectors on the device.
+// Build the request's matrix and vectors on the device (builder thread).
 mapi_status build(Server* sv, ServeReq* q) {
-  mapi_ctx* c = sv->child;
+  mapi_ctx* c = sv->bchild;
   const mapi_request& r = q->r;
   mapi_status s;
   if (r.kind == MAPI_REQ_PCA) {
@@ -444,23 +458,43 @@ void run_round(Server* sv) {
   }
 }
 
+// A queued request fits now (resident bytes and slots).
+bool admissible(const Server* sv) {
+  return !sv->queue.empty() && sv->resident < sv->parent->max_slots &&
+         sv->used + sv->queue.front()->need <= sv->budget;
+}
+
 void loop(Server* sv) {
   cudaSetDevice(sv->child->device);
   for (;;) {
-    std::vector<ServeReq*> admit, dropped;
+    std::vector<ServeReq*> ready, dropped;
     {
       std::unique_lock<std::mutex> lock(sv->mu);
-      sv->cv.wait(lock, [&] { return sv->stop || !sv->queue.empty() || !sv->live.empty(); });
+      sv->cv.wait(lock, [&] {
+        return sv->stop || admissible(sv) || !sv->live.empty() || !sv->built.empty();
+      });
       if (sv->stop) break;
-      while (!sv->queue.empty() && sv->resident < sv->parent->max_slots &&
-             sv->used + sv->queue.front()->need <= sv->budget) {
+      // admission: the builder takes it from here
+      bool any = false;
+      while (admissible(sv)) {
         ServeReq* q = sv->queue.front();
         sv->queue.pop_front();
         sv->used += q->need;
         sv->resident += 1;
         q->state = 1;
-        admit.push_back(q);
+        q->t_admit = Clock::now();
+        sv->to_build.push_back(q);
+        any = true;
       }
+      if (any) sv->bcv.notify_all();
+      while (!sv->built.empty()) {
+        ready.push_back(sv->built.front());
+        sv->built.pop_front();
+      }
+    }
+    for (ServeReq* q : ready) sv->live.push_back(q);
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
       for (ServeReq* q : sv->live)
         if (q->cancel) dropped.push_back(q);
     }
@@ -468,27 +502,70 @@ void loop(Server* sv) {
       sv->live.erase(std::find(sv->live.begin(), sv->live.end(), q));
       finish(sv, q, MAPI_ECANCELLED);
     }
-    for (ServeReq* q : admit) {
-      q->t_admit = Clock::now();
-      const mapi_status s = build(sv, q);
-      if (s == MAPI_OK && cudaStreamSynchronize(sv->child->stream) != cudaSuccess) {
-        cudaGetLastError();
-        finish(sv, q, MAPI_ECUDA);
-        continue;
-      }
-      q->t_built = Clock::now();
-      if (s != MAPI_OK) finish(sv, q, s);
-      else sv->live.push_back(q);
-    }
     if (!sv->live.empty()) run_round(sv);
   }
   // shutting down: everything still resident is dropped
   for (ServeReq* q : sv->live) {
-    release(sv, q);
+    release(sv, q, false);
     q->state = 2;
   }
   sv->live.clear();
   cudaStreamSynchronize(sv->child->stream);
+}
+
+// Builder thread: uploads and builds admitted requests on its own context
+// and stream while the loop runs rounds, and frees finished matrices.
+void builder(Server* sv) {
+  cudaSetDevice(sv->bchild->device);
+  for (;;) {
+    ServeReq* q = nullptr;
+    std::vector<mapi_mat*> frees;
+    {
+      std::unique_lock<std::mutex> lock(sv->mu);
+      sv->bcv.wait(lock, [&] {
+        return sv->bstop || !sv->to_build.empty() || !sv->to_free.empty();
+      });
+      frees.swap(sv->to_free);
+      if (!sv->bstop && !sv->to_build.empty()) {
+        q = sv->to_build.front();
+        sv->to_build.pop_front();
+      }
+    }
+    for (mapi_mat* m : frees) mapi_matrix_free(sv->bchild, m);
+    if (!q) {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      if (sv->bstop && sv->to_free.empty()) break;
+      continue;
+    }
+    bool cancelled;
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      cancelled = q->cancel;
+    }
+    if (cancelled) {
+      finish(sv, q, MAPI_ECANCELLED, true);
+      continue;
+    }
+    mapi_status s = build(sv, q);
+    if (s == MAPI_OK && cudaStreamSynchronize(sv->bchild->stream) != cudaSuccess) {
+      cudaGetLastError();
+      s = MAPI_ECUDA;
+    }
+    if (s != MAPI_OK) {
+      finish(sv, q, s, true);
+      continue;
+    }
+    q->t_built = Clock::now();
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      sv->built.push_back(q);
+    }
+    sv->cv.notify_all();
+  }
+  // requests admitted but never built
+  std::lock_guard<std::mutex> lock(sv->mu);
+  for (ServeReq* q : sv->to_build) q->state = 2;
+  sv->to_build.clear();
 }
 
 mapi_status ensure_server(mapi_ctx* ctx, Server** out) {
@@ -501,6 +578,11 @@ mapi_status ensure_server(mapi_ctx* ctx, Server** out) {
     cfg.device = ctx->device;
     mapi_status s = mapi_create(&cfg, &sv->child);
     if (s != MAPI_OK) {
+      delete sv;
+      return s;
+    }
+    if ((s = mapi_create(&cfg, &sv->bchild)) != MAPI_OK) {
+      mapi_destroy(sv->child);
       delete sv;
       return s;
     }
@@ -532,6 +614,7 @@ mapi_status ensure_server(mapi_ctx* ctx, Server** out) {
       sv->budget = fr / 10 * 8;
     }
     sv->th = std::thread(loop, sv);
+    sv->bth = std::thread(builder, sv);
     ctx->server = sv;
   }
   *out = ctx->server;
@@ -554,11 +637,21 @@ void server_shutdown(mapi_ctx* ctx) {
   }
   sv->cv.notify_all();
   if (sv->th.joinable()) sv->th.join();
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->bstop = true;
+  }
+  sv->bcv.notify_all();
+  if (sv->bth.joinable()) sv->bth.join();
+  // requests the builder held or had built: their buffers go with the contexts
+  for (ServeReq* q : sv->built) release(sv, q, true);
+  sv->built.clear();
   for (auto& kv : sv->tickets) delete kv.second;
   if (sv->round_start) cudaEventDestroy(sv->round_start);
   if (sv->batch_stream) cudaStreamDestroy(sv->batch_stream);
   if (sv->wide_ctl) cudaFreeHost(sv->wide_ctl);
   mapi_destroy(sv->child);
+  mapi_destroy(sv->bchild);
   delete sv;
 }
 
