@@ -37,6 +37,8 @@ __all__ = [
     "small_grid_matrix",
     "wishart_instance_device",
     "barabasi_albert_digraph_fast",
+    "stochastic_pca_data",
+    "minibatches",
 ]
 
 DEFAULT_SPIKES = (50.0, 30.0, 20.0, 10.0, 5.0, 4.0, 3.0, 2.0)
@@ -205,3 +207,21 @@ def barabasi_albert_digraph_fast(n: int, m: int = 8, seed: int = 0):
     indptr = np.zeros(n + 1, dtype=np.int64)
     indptr[m + 1:] = np.arange(1, n - m + 1, dtype=np.int64) * m
     return indptr.astype(np.int32), targets.ravel().astype(np.int32)
+
+
+def stochastic_pca_data(N: int = 10 ** 6, D: int = 10, seed: int = 0,
+                        dtype=np.float32) -> np.ndarray:
+    """X = U diag(1, sqrt(0.9), ..., sqrt(0.9)) V^T (N x D, rows are samples),
+    U an N x D random orthonormal basis and V a random D x D orthogonal matrix
+    (QR of Gaussians), so X^T X has eigenvalues 1, 0.9, ...: the synthetic
+    set of the §3.2 comparison with the stochastic power method."""
+    r = rng(seed)
+    U, _ = np.linalg.qr(r.standard_normal((N, D)))
+    V, _ = np.linalg.qr(r.standard_normal((D, D)))
+    sig = np.sqrt(np.array([1.0] + [0.9] * (D - 1)))[:D]
+    return np.ascontiguousarray(((U * sig) @ V.T).astype(dtype))
+
+
+def minibatches(N: int, T: int, s: int, seed: int = 0) -> np.ndarray:
+    """T x s sample indices drawn uniformly with replacement (Alg. 3 step 3)."""
+    return rng(seed).integers(0, N, size=(T, s)).astype(np.int32)

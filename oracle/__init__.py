@@ -67,6 +67,7 @@ def _get():
                 "or_pca_topk": (i, [i, i, p, l, l, l, l, i, d, d, p, l, p, l, p]),
                 "or_google_matrix": (None, [l, p, p, d, p]),
                 "or_pagerank_sparse": (i, [i, l, p, p, d, i, p, i, d, p, p, p]),
+                "or_minibatch_momentum": (i, [i, p, l, l, p, i, i, d, p, i, p]),
                 "or_round_bf16": (d, [d]),
                 "or_round_e4m3": (d, [d]),
                 "or_fp8_row_exponent": (i, [p, l]),
@@ -241,6 +242,20 @@ def pagerank_sparse(op, n: int, indptr, indices, w0, iters: int, alpha: float = 
                                    1 if round32 else 0, _ptr(w0), int(iters), float(tol),
                                    _ptr(w), C.byref(it), C.byref(dl))
     return st, w, it.value, dl.value
+
+
+def minibatch_momentum(op, X, batch, beta: float, w0, final_l2: bool = True):
+    """Mini-batch MAPI with momentum (Alg. 3).  X: N x D samples (rows);
+    batch: T x s sample indices (the draws of step 3).  Returns (status, w)."""
+    X = _f64(X)
+    N, D = X.shape
+    b = np.ascontiguousarray(np.asarray(batch, dtype=np.int32))
+    T, s = b.shape
+    w0 = _f64(w0)
+    w = np.empty(D)
+    st = _get().or_minibatch_momentum(_op(op), _ptr(X), N, D, _ptr(b), T, s, float(beta),
+                                      _ptr(w0), FINAL_L2 if final_l2 else 0, _ptr(w))
+    return st, w
 
 
 def round_bf16(x) -> np.ndarray:

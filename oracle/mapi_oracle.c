@@ -451,6 +451,64 @@ int or_pagerank_sparse(int op, long n, const int* indptr, const int* indices,
   return status;
 }
 
+/*
+ * Mini-batch MAPI with momentum (Alg. 3), on data X (N x D, row-major: one
+ * sample per row).  The mini-batches are given: batch[t * s + i] is the i-th
+ * sample of step t (Alg. 3 step 3 draws them; the caller passes the draws).
+ *   step 1: w_0 = w0 / ||w0||_2 (reading of the unnamed norm, as in Alg. 1),
+ *           w_{-1} = 0;
+ *   step 4: A_t = (1/s) sum_i x_{t_i} (+) x_{t_i}^T (entries term(x_p, x_q),
+ *           summed over the batch in order, then divided by s);
+ *           v = A_t (+) w_t - beta w_{t-1}  (rows of A_t against w_t);
+ *   step 5: w_{t+1} = v / ||v||_1, w_t = w_t / ||v||_1 (the l2 norm for
+ *           op = dot: the momentum power method of the comparison);
+ *   step 7 (OR_FINAL_L2): w_T / ||w_T||_2.
+ */
+int or_minibatch_momentum(int op, const double* X, long N, long D, const int* batch, int T,
+                          int s, double beta, const double* w0, int flags, double* w_out) {
+  if (N <= 0 || D <= 0 || T < 0 || s <= 0) return OR_EINVAL;
+  double* w = (double*)malloc(sizeof(double) * D);
+  double* wp = (double*)malloc(sizeof(double) * D);
+  double* v = (double*)malloc(sizeof(double) * D);
+  double* A = (double*)malloc(sizeof(double) * D * D);
+  int status = OR_OK;
+  for (long p = 0; p < D; ++p) { w[p] = w0[p]; wp[p] = 0.0; }
+  {
+    double n2 = or_norm2(w, D);
+    if (n2 == 0.0) status = OR_EZERONORM;
+    else for (long p = 0; p < D; ++p) w[p] = w[p] / n2;
+  }
+  for (int t = 0; t < T && status == OR_OK; ++t) {
+    for (long p = 0; p < D; ++p)
+      for (long q = 0; q < D; ++q) {
+        double a = 0.0;
+        for (int i = 0; i < s; ++i) {
+          long k = batch[(long)t * s + i];
+          if (k < 0 || k >= N) { status = OR_EINVAL; break; }
+          a += or_term(op, X[k * D + p], X[k * D + q]);
+        }
+        A[p * D + q] = a / (double)s;
+      }
+    if (status != OR_OK) break;
+    for (long p = 0; p < D; ++p) v[p] = or_vecprod(op, A + p * D, w, D) - beta * wp[p];
+    double L = (op == OP_DOT) ? or_norm2(v, D) : or_norm1(v, D);
+    if (!isfinite(L)) { status = OR_ENONFINITE; break; }
+    if (L == 0.0) { status = OR_EZERONORM; break; }
+    for (long p = 0; p < D; ++p) {
+      wp[p] = w[p] / L;
+      w[p] = v[p] / L;
+    }
+  }
+  if (status == OR_OK && (flags & OR_FINAL_L2)) {
+    double n2 = or_norm2(w, D);
+    if (n2 == 0.0) status = OR_EZERONORM;
+    else for (long p = 0; p < D; ++p) w[p] = w[p] / n2;
+  }
+  for (long p = 0; p < D; ++p) w_out[p] = w[p];
+  free(w); free(wp); free(v); free(A);
+  return status;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Storage formats.  The paper fixes no storage; these follow the format    */
 /* definitions (IEEE-754 round-to-nearest-even) so that the oracle can run  */

@@ -545,3 +545,43 @@ def test_sparse_pagerank_stop_rule():
     st2, got, it2, dl2 = oracle.pagerank_sparse("min1", 200, ip, ix, w0, 500, tol=1e-9)
     assert st == st2 == oracle.OK and it == it2 < 500 and dl2 < 1e-9
     np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("op", ["min1", "min2", "dot"])
+def test_minibatch_momentum_full_batch_without_momentum_is_alg1(op):
+    """Alg. 3 with beta = 0 and every sample in every batch is Alg. 1 on the
+    min-covariance (1/N) sum_k x_k (+) x_k^T of Eq. (5)."""
+    N, D, T = 50, 6, 12
+    X = datagen.stochastic_pca_data(N, D, seed=70).astype(np.float64)
+    batch = np.tile(np.arange(N, dtype=np.int32), (T, 1))
+    w0 = datagen.start_vector(D, seed=71).astype(np.float64)
+    st, got = oracle.minibatch_momentum(op, X, batch, 0.0, w0)
+    C = oracle.mincov(op, X.T.copy(), float(N))
+    st2, want, _, _ = oracle.mapi(op, C, w0, T, final_l2=True)
+    assert st == st2 == oracle.OK
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+
+
+def test_minibatch_momentum_dot_is_the_momentum_polynomial():
+    """With op = dot and full batches, w_t is p_t(C) w_0 up to scale, where
+    p_{t+1}(x) = x p_t(x) - beta p_{t-1}(x), p_0 = 1, p_{-1} = 0 (the
+    recurrence of the momentum power method), evaluated on eigh(C)."""
+    N, D, T, beta = 80, 7, 25, 0.2
+    X = datagen.stochastic_pca_data(N, D, seed=72).astype(np.float64)
+    batch = np.tile(np.arange(N, dtype=np.int32), (T, 1))
+    w0 = datagen.start_vector(D, seed=73).astype(np.float64)
+    st, got = oracle.minibatch_momentum("dot", X, batch, beta, w0)
+    lam, Q = np.linalg.eigh(X.T @ X / N)
+    p_prev, p = np.zeros(D), np.ones(D)
+    for _ in range(T):
+        p_prev, p = p, lam * p - beta * p_prev
+    want = Q @ (p * (Q.T @ w0))
+    want /= np.linalg.norm(want)
+    assert st == oracle.OK
+    np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-12)
+
+
+def test_minibatch_sample_data_spectrum():
+    X = datagen.stochastic_pca_data(2000, 10, seed=74).astype(np.float64)
+    lam = np.sort(np.linalg.eigvalsh(X.T @ X))[::-1]
+    np.testing.assert_allclose(lam, [1.0] + [0.9] * 9, rtol=1e-6)  # FP32 samples
