@@ -188,6 +188,44 @@ mapi_status mapi_iterate(mapi_ctx* ctx, const mapi_mat* A, mapi_op op,
                          int* iters_done, double* last_delta);
 
 /*
+ * MAPI, then regular power iteration (the switch §3.2 suggests when the
+ * eigenvector itself is wanted): Alg. 1 with op (MIN1, MIN2 or DIAMOND) from
+ * w0 for up to mapi_iters steps or until its delta < mapi_tol; its last
+ * iterate is the start vector (scaled to unit l2 norm, Alg. 1 step 1) of
+ * Eq. (1)'s iteration for up to rpi_iters steps or until delta < rpi_tol.
+ *   A: square float storage.  w0, w_out: device n FP32 (caller-owned).
+ *   flags: MAPI_FLAG_RAW_START applies to the first phase, MAPI_FLAG_FINAL_L2
+ *     to the result (the second phase already ends l2-normalised).
+ *   iters_done, last_delta: host arrays of 2 (phase 1, phase 2), may be NULL.
+ * Errors: MAPI_EINVAL; a status of the first phase (then w_out holds its last
+ * good iterate) or of the second; MAPI_ECUDA.  Synchronous.
+ */
+mapi_status mapi_iterate_switch(mapi_ctx* ctx, const mapi_mat* A, mapi_op op, const float* w0,
+                                int mapi_iters, double mapi_tol, int rpi_iters, double rpi_tol,
+                                unsigned flags, float* w_out, int* iters_done,
+                                double* last_delta);
+
+/*
+ * Mini-batch MAPI with momentum, Alg. 3 (and, with MAPI_OP_DOT, the
+ * momentum power method it is set against in §3.2), one CTA for all steps.
+ *   X      device, N x D row-major FP32 (rows are samples), 1 <= D <= 128.
+ *   batch  device, T x s row-major int32 (NULL when T = 0): the s sample
+ *          indices of step t
+ *          (Alg. 3 step 3 draws them; the caller passes the draws).
+ *   Step 1: w_0 = w0 / ||w0||_2, w_{-1} = 0.  Step t: A_t = (1/s) sum over
+ *   the batch of x (+) x^T, v = A_t (+) w_t - beta w_{t-1}, then
+ *   w_{t+1} = v / L and w_t / L for the momentum term, L = ||v||_1
+ *   (||v||_2 for DOT).  After T steps w_T goes to w_out, scaled to unit l2
+ *   norm if MAPI_FLAG_FINAL_L2.
+ *   op: MIN1, MIN2 or DOT.  w0, w_out: device D FP32 (caller-owned).
+ * Errors: MAPI_EINVAL (shape, op, an index outside [0, N)), MAPI_EZERONORM,
+ * MAPI_ENONFINITE (the step's norm), MAPI_ECUDA.  Synchronous.
+ */
+mapi_status mapi_minibatch_momentum(mapi_ctx* ctx, const float* X, int N, int D,
+                                    const int* batch, int T, int s, double beta, mapi_op op,
+                                    const float* w0, unsigned flags, float* w_out);
+
+/*
  * Min-covariance matrix, Eq. (5): C = (1/denom) X (+) X^T for a packed
  * X (D x N, columns are samples); op MIN1, MIN2 or DOT (then C is the
  * ordinary covariance of Eq. (2)).  Eq. (5) uses denom = N, Alg. 2 step 4

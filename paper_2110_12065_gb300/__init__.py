@@ -25,7 +25,8 @@ __all__ = [
     "mapi_pca_topk", "mapi_google_matrix", "mapi_pagerank", "mapi_profile",
     "mapi_get_stats", "mapi_iterate_noalloc", "mapi_iterate_batched",
     "mapi_autotune_batched", "mapi_submit", "mapi_poll", "mapi_cancel",
-    "mapi_pagerank_sparse", "KERNEL_CLASSES",
+    "mapi_pagerank_sparse", "mapi_iterate_switch", "mapi_minibatch_momentum",
+    "KERNEL_CLASSES",
     "OP", "ST", "FLAG_FINAL_L2", "FLAG_RAW_START", "SCALE_AUTO",
     "PCA_MINCOV", "PCA_PAIR", "STATUS",
 ]
@@ -109,6 +110,8 @@ def load(path: str | None = None):
         "mapi_matrix_download": [p_, p_, p_, p_],
         "mapi_iterate": [p_, p_, i, i, p_, i64, i, d, u, p_, p_, p_],
         "mapi_mincov": [p_, p_, i, d, p_],
+        "mapi_iterate_switch": [p_, p_, i, p_, i, d, i, d, u, p_, p_, p_],
+        "mapi_minibatch_momentum": [p_, p_, i, i, p_, i, i, d, i, p_, u, p_],
         "mapi_pca_topk": [p_, p_, i, i, i, i, d, d, p_, p_, p_],
         "mapi_google_matrix": [p_, p_, p_, i, d, i, C.POINTER(p_)],
         "mapi_pagerank": [p_, p_, p_, i, d, i, i, p_, i, d, p_, p_, p_],
@@ -257,6 +260,47 @@ def mapi_iterate(ctx, A, op, w0, max_iters: int, tol_l1: float = 0.0,
     res = (w_out.reshape(-1) if squeeze else w_out, list(it), list(dl))
     _check(st, "mapi_iterate", ctx, partial=res)
     return res
+
+
+def mapi_iterate_switch(ctx, A, op, w0, mapi_iters: int, rpi_iters: int,
+                        mapi_tol: float = 0.0, rpi_tol: float = 0.0, flags: int = 0,
+                        w_out=None):
+    """MAPI for up to mapi_iters steps, then regular power iteration from its
+    iterate.  Returns (w (n,), [iters MAPI, iters RPI], [delta MAPI, delta RPI])."""
+    torch = _torch()
+    if w_out is None:
+        w_out = torch.empty_like(w0)
+    opi = OP[op] if isinstance(op, str) else int(op)
+    it = (C.c_int * 2)()
+    dl = (C.c_double * 2)()
+    st = load().mapi_iterate_switch(ctx, A, opi, C.c_void_p(_dptr(w0)), int(mapi_iters),
+                                    float(mapi_tol), int(rpi_iters), float(rpi_tol), int(flags),
+                                    C.c_void_p(_dptr(w_out)), it, dl)
+    res = (w_out, list(it), list(dl))
+    _check(st, "mapi_iterate_switch", ctx, partial=res)
+    return res
+
+
+def mapi_minibatch_momentum(ctx, X, batch, beta: float, op, w0, flags: int = 0,
+                            w_out=None):
+    """Alg. 3 over the sample draws in batch.  X: torch CUDA float32 (N, D);
+    batch: torch CUDA int32 (T, s); w0: CUDA float32 (D,).  Returns w_out."""
+    torch = _torch()
+    if X.dtype != torch.float32 or batch.dtype != torch.int32:
+        raise ValueError("X float32, batch int32")
+    X = X.contiguous()
+    batch = batch.contiguous()
+    N, D = X.shape
+    T, s = batch.shape
+    if w_out is None:
+        w_out = torch.empty_like(w0)
+    opi = OP[op] if isinstance(op, str) else int(op)
+    st = load().mapi_minibatch_momentum(ctx, C.c_void_p(_dptr(X)), int(N), int(D),
+                                        C.c_void_p(_dptr(batch)), int(T), int(s), float(beta),
+                                        opi, C.c_void_p(_dptr(w0)), int(flags),
+                                        C.c_void_p(_dptr(w_out)))
+    _check(st, "mapi_minibatch_momentum", ctx, partial=w_out)
+    return w_out
 
 
 def mapi_mincov(ctx, X, op, denom: float, C_out=None):

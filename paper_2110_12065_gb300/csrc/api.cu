@@ -293,6 +293,16 @@ uint64_t fbits(double d) {
 
 }  // namespace
 
+namespace {
+// Keeps the first phase's state of a switched solve and stops the second
+// phase when the first failed.
+__global__ void k_keep_phase(const IterCtl* ctl, VecState* keep, int* abort) {
+  const VecState st = ctl->v[0];
+  *keep = st;
+  *abort = st.status != MAPI_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char* mapi_status_str(mapi_status s) {
@@ -367,7 +377,8 @@ mapi_status mapi_destroy(mapi_ctx* ctx) {
   std::set<mapi_mat*> ms = ctx->mats;
   for (auto* m : ms) free_matrix(ctx, m);
   for (DevBuf* b : {&ctx->ypart, &ctx->wbuf0, &ctx->wbuf1, &ctx->ctl, &ctx->aux, &ctx->mcpart,
-                    &ctx->pca_c0, &ctx->pca_c1, &ctx->pca_q, &ctx->pca_defl, &ctx->batch})
+                    &ctx->pca_c0, &ctx->pca_c1, &ctx->pca_q, &ctx->pca_defl, &ctx->batch,
+                    &ctx->hyb})
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
@@ -521,6 +532,86 @@ mapi_status mapi_iterate(mapi_ctx* ctx, const mapi_mat* A, mapi_op op, int nvec,
   return result;
 }
 
+
+mapi_status mapi_iterate_switch(mapi_ctx* ctx, const mapi_mat* A, mapi_op op, const float* w0,
+                                int mapi_iters, double mapi_tol, int rpi_iters, double rpi_tol,
+                                unsigned flags, float* w_out, int* iters_done,
+                                double* last_delta) {
+  if (!ctx) return MAPI_EINVAL;
+  if (!valid_matrix(ctx, A)) return fail(ctx, MAPI_EINVAL, "unknown matrix");
+  if (A->rows != A->cols) return fail(ctx, MAPI_EINVAL, "MAPI needs a square matrix");
+  if (!w0 || !w_out || mapi_iters < 0 || rpi_iters < 0)
+    return fail(ctx, MAPI_EINVAL, "bad vector arguments");
+  if (op != MAPI_OP_MIN1 && op != MAPI_OP_MIN2 && op != MAPI_OP_DIAMOND)
+    return fail(ctx, MAPI_EINVAL, "the first phase takes MIN1, MIN2 or DIAMOND");
+  if (is_int_storage(A->storage)) return fail(ctx, MAPI_EINVAL, "float storage only");
+  if (op == MAPI_OP_DIAMOND && A->storage != MAPI_ST_F32)
+    return fail(ctx, MAPI_EINVAL, "DIAMOND needs F32 storage");
+  DeviceGuard g(ctx->device);
+  mapi_status s = prepare_solve(ctx, A, 1);
+  if (s != MAPI_OK) return s;
+  const int64_t n = A->rows;
+  if ((s = ensure(ctx, ctx->hyb, 256 + sizeof(float) * n)) != MAPI_OK) return s;
+  VecState* keep = (VecState*)ctx->hyb.p;
+  int* abort = (int*)((char*)ctx->hyb.p + 128);
+  float* mid = (float*)((char*)ctx->hyb.p + 256);
+  std::vector<int64_t> key = {3,
+                              (int64_t)A->id,
+                              (int64_t)op,
+                              (int64_t)(uintptr_t)w0,
+                              mapi_iters,
+                              (int64_t)fbits(mapi_tol),
+                              rpi_iters,
+                              (int64_t)fbits(rpi_tol),
+                              (int64_t)flags,
+                              (int64_t)(uintptr_t)w_out,
+                              (int64_t)(uintptr_t)ctx->wbuf0.p,
+                              (int64_t)(uintptr_t)ctx->ypart.p,
+                              (int64_t)(uintptr_t)ctx->hyb.p,
+                              (int64_t)ctx->prof_on};
+  GraphEntry* ge = nullptr;
+  s = launch_cached_graph(
+      ctx, key,
+      [&](cudaStream_t cs) -> mapi_status {
+        // MAPI first (Alg. 1), its last iterate handed to regular power
+        // iteration (Eq. (1)) for the final convergence
+        mapi_status r = enqueue_solve(ctx, cs, A, op, 1, w0, n, mapi_iters, mapi_tol,
+                                      flags & MAPI_FLAG_RAW_START, mid, n);
+        if (r != MAPI_OK) return r;
+        k_keep_phase<<<1, 1, 0, cs>>>((const IterCtl*)ctx->ctl.p, keep, abort);
+        MAPI_CUDA_TRY(ctx, cudaGetLastError());
+        count_launch(ctx);
+        return enqueue_solve(ctx, cs, A, MAPI_OP_DOT, 1, mid, n, rpi_iters, rpi_tol,
+                             flags & MAPI_FLAG_FINAL_L2, w_out, n, abort);
+      },
+      &ge);
+  if (s != MAPI_OK) return s;
+  VecState first;
+  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(&first, keep, sizeof(VecState), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ctl_host, ctx->ctl.p, sizeof(IterCtl),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+  MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  finish_graph(ctx, ge);
+  const VecState& second = ctx->ctl_host->v[0];
+  if (iters_done) {
+    iters_done[0] = first.iters;
+    iters_done[1] = first.status == MAPI_OK ? second.iters : 0;
+  }
+  if (last_delta) {
+    last_delta[0] = (double)first.delta;
+    last_delta[1] = first.status == MAPI_OK ? (double)second.delta : NAN;
+  }
+  if (first.status != MAPI_OK) {
+    // the MAPI phase failed: its last good iterate is the result
+    MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(w_out, mid, sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                                       ctx->stream));
+    MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return fail(ctx, (mapi_status)first.status, "the MAPI phase stopped early");
+  }
+  if (second.status != MAPI_OK) return fail(ctx, (mapi_status)second.status, "the RPI phase failed");
+  return MAPI_OK;
+}
 
 mapi_status mapi_mincov(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, double denom,
                         float* C_out) {

@@ -117,6 +117,7 @@ struct mapi_ctx {
   DevBuf pca_c0, pca_c1, pca_q, pca_defl;  // PCA scratch (covariances, deflation)
   int* rec_host = nullptr;                 // pinned: per-component steps and statuses
   DevBuf batch;                            // batched solves: instance table and results
+  DevBuf hyb;                              // MAPI -> RPI switch: the handed-over iterate
   int batch_rows_per_warp[2][2] = {{2, 2}, {2, 2}};  // [F32, BF16][1, 4 vectors], autotuned
   mapi::IterCtl* ctl_host = nullptr;  // pinned mirror of the control block
 

@@ -289,3 +289,60 @@ def test_full_size_one_step_f32(mapi_ctx):
         assert rel_l1(w, y / np.abs(y).sum()) <= TOL32
     finally:
         M.mapi_matrix_free(mapi_ctx, mat)
+
+
+@pytest.mark.parametrize("op", ["min1", "min2", "diamond"])
+def test_switch_to_rpi_equals_the_two_phases(mapi_ctx, op):
+    """MAPI then regular power iteration from its iterate (§3.2)."""
+    n = 300
+    A = datagen.symmetric_gaussian(n, seed=60).astype(np.float32)
+    if op == "min2":
+        A = np.abs(A)
+    w0 = datagen.start_vector(n, seed=61)
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(A), "f32")
+    try:
+        w, it, dl = M.mapi_iterate_switch(mapi_ctx, mat, op, to_dev(w0), 20, 40)
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
+    Ad = A.astype(np.float64)
+    st, mid, it1, _ = oracle.mapi(op, Ad, w0.astype(np.float64), 20)
+    st2, want, it2, _ = oracle.mapi("dot", Ad, mid, 40)
+    assert it == [it1, it2] == [20, 40]
+    assert rel_l1(to_host(w), want) <= 1e-5
+
+
+def test_switch_reaches_the_eigenvector(mapi_ctx):
+    """The RPI phase converges to the dominant eigenvector; MAPI alone stops at
+    a nearby pseudo-eigenvector."""
+    n = 200
+    r = datagen.rng(62)
+    Q, _ = np.linalg.qr(r.standard_normal((n, n)))
+    lam = np.concatenate([[10.0, 5.0], r.uniform(0.0, 2.0, size=n - 2)])
+    A = ((Q * lam) @ Q.T).astype(np.float32)
+    w0 = datagen.start_vector(n, seed=63)
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(A), "f32")
+    try:
+        w, it, dl = M.mapi_iterate_switch(mapi_ctx, mat, "min1", to_dev(w0), 50, 200,
+                                          rpi_tol=1e-7)
+        wm, _, _ = M.mapi_iterate(mapi_ctx, mat, "min1", to_dev(w0), 50, flags=M.FLAG_FINAL_L2)
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
+    u = np.linalg.eigh(A.astype(np.float64))[1][:, -1]
+    got = to_host(w).astype(np.float64)
+    err = 1.0 - (got @ u) ** 2
+    err_mapi = 1.0 - (to_host(wm).astype(np.float64) @ u) ** 2
+    assert it[0] == 50 and it[1] < 200 and dl[1] < 1e-7
+    assert err < 1e-6 and err < err_mapi
+
+
+def test_switch_reports_a_failed_first_phase(mapi_ctx):
+    A = np.zeros((40, 40), np.float32)
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(A), "f32")
+    try:
+        with pytest.raises(M.MapiError) as e:
+            M.mapi_iterate_switch(mapi_ctx, mat, "min1", to_dev(datagen.start_vector(40, 64)),
+                                  10, 10)
+        assert e.value.name == "EZERONORM"
+        assert e.value.partial[1][1] == 0
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
