@@ -17,7 +17,10 @@ Workload shapes follow the paper's experiments:
   kind (power-law in-degree) stands in for them;
 * symmetric positive semi-definite Wishart instances of mixed sizes for
   batched runs;
-* start vectors drawn uniformly (Alg. 1 step 1 asks for a random w0).
+* start vectors drawn uniformly (Alg. 1 step 1 asks for a random w0);
+* occluded versions of a synthetic gray-scale image for the reconstruction of
+  Alg. 2 (§3.1: 16 tiles, 3 of them replaced by uniform noise); the paper's
+  photographs are not available.
 """
 from __future__ import annotations
 
@@ -39,6 +42,8 @@ __all__ = [
     "barabasi_albert_digraph_fast",
     "stochastic_pca_data",
     "minibatches",
+    "clean_image",
+    "occluded_images",
 ]
 
 DEFAULT_SPIKES = (50.0, 30.0, 20.0, 10.0, 5.0, 4.0, 3.0, 2.0)
@@ -225,3 +230,35 @@ def stochastic_pca_data(N: int = 10 ** 6, D: int = 10, seed: int = 0,
 def minibatches(N: int, T: int, s: int, seed: int = 0) -> np.ndarray:
     """T x s sample indices drawn uniformly with replacement (Alg. 3 step 3)."""
     return rng(seed).integers(0, N, size=(T, s)).astype(np.int32)
+
+
+def clean_image(side: int = 128, seed: int = 0) -> np.ndarray:
+    """A smooth side x side gray-scale image in [0, 1] (float32): a soft
+    gradient plus a few Gaussian blobs of random place, width and sign."""
+    r = rng(seed)
+    yy, xx = np.mgrid[0:side, 0:side].astype(np.float64) / max(side - 1, 1)
+    img = 0.35 + 0.25 * (xx * r.uniform(-1, 1) + yy * r.uniform(-1, 1))
+    for _ in range(6):
+        cx, cy = r.uniform(0.1, 0.9, 2)
+        sw = r.uniform(0.05, 0.2)
+        img += r.uniform(-0.35, 0.35) * np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * sw * sw))
+    return np.clip(img, 0.0, 1.0).astype(np.float32)
+
+
+def occluded_images(side: int = 128, N: int = 10, grid: int = 4, n_occ: int = 3,
+                    seed: int = 0):
+    """(clean (side x side), corrupted (N x side x side)): each of the N
+    versions has n_occ of its grid x grid tiles (chosen without repetition)
+    replaced by i.i.d. U[0, 1] pixels (§3.1: 32 x 32 tiles of a 128 x 128
+    image, 3 of 16 replaced).  side must be a multiple of grid."""
+    if side % grid:
+        raise ValueError("side must be a multiple of grid")
+    clean = clean_image(side, seed)
+    r = rng(seed + 1)
+    t = side // grid
+    out = np.repeat(clean[None], N, axis=0)
+    for i in range(N):
+        for tile in r.choice(grid * grid, size=n_occ, replace=False):
+            ty, tx = divmod(int(tile), grid)
+            out[i, ty * t:(ty + 1) * t, tx * t:(tx + 1) * t] = r.uniform(0, 1, (t, t))
+    return clean, out.astype(np.float32)

@@ -63,6 +63,7 @@ def _get():
                 "or_mavp_outer": (None, [i, p, l, p]),
                 "or_deflate": (None, [i, p, l, p, l, l, p]),
                 "or_deflate_vec": (None, [i, p, l, p, l, l]),
+                "or_reconstruct": (None, [i, p, l, l, l, p, l, l, p, p, l]),
                 "or_pair_step": (None, [i, p, l, l, l, p, d, p]),
                 "or_pca_topk": (i, [i, i, p, l, l, l, l, i, d, d, p, l, p, l, p]),
                 "or_google_matrix": (None, [l, p, p, d, p]),
@@ -209,6 +210,34 @@ def pca_topk(mode, op, X, k: int, iters: int, denom: float, W0,
                             float(tol), float(denom), _ptr(W0), D, _ptr(P), D,
                             _ptr(its))
     return int(st), P, its
+
+
+def reconstruct(op, W, V, m) -> np.ndarray:
+    """Alg. 2 step 8 for every column v_i of V (D x N): (W (+) W^T)(v_i - m) + m,
+    R_pq = sum_c term(W_pc, W_qc), the product with v_i - m ordinary."""
+    V, m = _f64(V), _f64(m)
+    D, N = V.shape
+    W = np.asfortranarray(np.asarray(W, dtype=np.float64).reshape(D, -1))
+    out = np.empty((D, N))
+    _get().or_reconstruct(_op(op), _ptr(W), D, W.shape[1], D, _ptr(V), N, N, _ptr(m),
+                          _ptr(out), N)
+    return out
+
+
+def image_reconstruct(op, images, k: int, iters: int, W0, tol: float = 0.0):
+    """Alg. 2 end to end on N images of P pixels (images: N x P, one image a
+    row, i.e. step 1's v_i).  Step 2: V = [v_1 ... v_N] (P x N); step 3: m the
+    row mean of V, V - m; step 4: C = (V - m) (+) (V - m)^T / (N - 1); steps
+    5-6: k components by MAPI on the deflated C (W0: P x k raw starts); step 8
+    for every i.  Returns (status, W (P x k), reconstructions (N x P), iters)."""
+    V = np.ascontiguousarray(_f64(images).T)
+    P, N = V.shape
+    m = V.mean(axis=1)
+    X = V - m[:, None]
+    st, W, its = pca_topk("mincov", op, X, k, iters, float(N - 1), W0, tol)
+    if st != OK:
+        return st, W, None, its
+    return st, W, reconstruct(op, W, V, m).T.copy(), its
 
 
 def google_matrix(n: int, indptr, indices, alpha: float = 0.85) -> np.ndarray:

@@ -191,22 +191,46 @@ void or_mavp_outer(int op, const double* w, long D, double* P) {
 }
 
 /*
+ * The vector an outer product w (+) w^T of Alg. 2 (steps 6 and 8) is formed
+ * from.  The components are kept at unit l2 norm (§2.2); the outer product
+ * takes each at the unit norm of its own iteration: the l1 norm for the
+ * MAVP operators (the normalisation of Eq. (8)), the l2 norm for the
+ * ordinary product (w w^T, the projector of §1).  A vector of equal
+ * magnitudes at unit l1 norm gives exactly the projector u u^T, u = w/||w||_2,
+ * under min1; at unit l2 norm it would give sqrt(D) u u^T.
+ */
+static void outer_vector(int op, const double* w, long D, double* out) {
+  double s = (op == OP_DOT) ? 1.0 : or_norm1(w, D);
+  for (long i = 0; i < D; ++i) out[i] = (s > 0.0) ? w[i] / s : w[i];
+}
+
+/* Q = sum_{m<k} wt_m (+) wt_m^T with wt_m = outer_vector(w_m). */
+static double* outer_sum(int op, long D, const double* W, long k, long ldw) {
+  double* Q = (double*)calloc((size_t)D * D, sizeof(double));
+  double* wt = (double*)malloc(sizeof(double) * (D > 0 ? D : 1));
+  for (long m = 0; m < k; ++m) {
+    outer_vector(op, W + m * ldw, D, wt);
+    for (long i = 0; i < D; ++i)
+      for (long j = 0; j < D; ++j) Q[i * D + j] += or_term(op, wt[i], wt[j]);
+  }
+  free(wt);
+  return Q;
+}
+
+/*
  * Deflation of a covariance for the k-th component (Alg. 2 step 6 generalised
  * with the sum form that follows Eq. (2)):
- *     C_k = (I - sum_{m<k} P_m) C,   P_m = w_m (+) w_m^T,
- * where the w_m are the earlier, l2-normalised components (§2.2: "normalize
- * the final w_t by its l2-norm for extraction of subsequent principal
- * vectors") and the juxtaposition P_m C is the ordinary matrix product.  With
- * op = dot this is the projection deflation (I - sum p_m p_m^T) C of §1.
+ *     C_k = (I - sum_{m<k} P_m) C,   P_m = wt_m (+) wt_m^T,
+ * where wt_m is the earlier component w_m (kept at unit l2 norm, §2.2) taken
+ * at the unit norm of its iteration (outer_vector: l1 for the MAVP
+ * operators, l2 for dot) and the juxtaposition P_m C is the ordinary matrix
+ * product.  With op = dot this is the projection deflation
+ * (I - sum p_m p_m^T) C of §1.
  * W holds the k earlier components as columns: W[i + m*ldw].
  */
 void or_deflate(int op, const double* C, long D, const double* W, long k,
                 long ldw, double* Ck) {
-  double* Q = (double*)calloc((size_t)D * D, sizeof(double));
-  for (long m = 0; m < k; ++m)
-    for (long i = 0; i < D; ++i)
-      for (long j = 0; j < D; ++j)
-        Q[i * D + j] += or_term(op, W[i + m * ldw], W[j + m * ldw]);
+  double* Q = outer_sum(op, D, W, k, ldw);
 #pragma omp parallel for schedule(static)
   for (long i = 0; i < D; ++i)
     for (long j = 0; j < D; ++j) {
@@ -221,12 +245,8 @@ void or_deflate(int op, const double* C, long D, const double* W, long k,
 void or_deflate_vec(int op, double* y, long D, const double* W, long k,
                     long ldw) {
   if (k <= 0) return;
-  double* Q = (double*)calloc((size_t)D * D, sizeof(double));
+  double* Q = outer_sum(op, D, W, k, ldw);
   double* z = (double*)malloc(sizeof(double) * D);
-  for (long m = 0; m < k; ++m)
-    for (long i = 0; i < D; ++i)
-      for (long j = 0; j < D; ++j)
-        Q[i * D + j] += or_term(op, W[i + m * ldw], W[j + m * ldw]);
   for (long i = 0; i < D; ++i) {
     double s = 0.0;
     for (long j = 0; j < D; ++j) s += Q[i * D + j] * y[j];
@@ -235,6 +255,39 @@ void or_deflate_vec(int op, double* y, long D, const double* W, long k,
   memcpy(y, z, sizeof(double) * D);
   free(z);
   free(Q);
+}
+
+/*
+ * Image reconstruction, Alg. 2 step 8: out_i = (W (+) W^T)(v_i - m) + m for
+ * the N columns v_i of V (D x N, leading dimension ldv).  W holds the k
+ * components as columns (W[p + c*ldw]), each taken at the unit norm of its
+ * iteration (outer_vector) as in step 6; R = W (+) W^T is the D x D matrix
+ * of the operator's matrix extension, rows of W against the columns of W^T:
+ * R_pq = sum_c term(Wt_pc, Wt_qc).  Its product with v_i - m is the ordinary
+ * one, as in the deflation of step 6.  Row p of R is formed when needed, so D
+ * may be large; out is D x N with leading dimension ldo.
+ */
+void or_reconstruct(int op, const double* W, long D, long k, long ldw,
+                    const double* V, long N, long ldv, const double* m,
+                    double* out, long ldo) {
+  double* Z = (double*)malloc(sizeof(double) * D * N);  /* v_i - m, row-major */
+  for (long q = 0; q < D; ++q)
+    for (long i = 0; i < N; ++i) Z[q * N + i] = V[q * ldv + i] - m[q];
+  double* Wt = (double*)malloc(sizeof(double) * (D * k > 0 ? D * k : 1));
+  for (long c = 0; c < k; ++c) outer_vector(op, W + c * ldw, D, Wt + c * D);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long p = 0; p < D; ++p) {
+    double* acc = (double*)calloc((size_t)N, sizeof(double));
+    for (long q = 0; q < D; ++q) {
+      double r = 0.0;
+      for (long c = 0; c < k; ++c) r += or_term(op, Wt[p + c * D], Wt[q + c * D]);
+      for (long i = 0; i < N; ++i) acc[i] += r * Z[q * N + i];
+    }
+    for (long i = 0; i < N; ++i) out[p * ldo + i] = acc[i] + m[p];
+    free(acc);
+  }
+  free(Wt);
+  free(Z);
 }
 
 /*

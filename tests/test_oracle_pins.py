@@ -310,17 +310,53 @@ def test_deflation_matches_prefix_form(op):
     W = r.standard_normal((D, 3))
     W /= np.linalg.norm(W, axis=0)
     Ck = oracle.deflate(op, Cm, W)
+    # the outer products take each component at unit l1 norm
+    Wt = W / np.abs(W).sum(axis=0)
     want = Cm.copy()
     for m in range(3):
         for col in range(D):
-            want[:, col] -= prefix_form(op, W[:, m], Cm[:, col])
+            want[:, col] -= prefix_form(op, Wt[:, m], Cm[:, col])
     np.testing.assert_allclose(Ck, want, rtol=1e-12, atol=1e-12)
     y = r.standard_normal(D)
     yk = oracle.deflate_vec(op, y, W)
-    want_y = y - sum(prefix_form(op, W[:, m], y) for m in range(3))
+    want_y = y - sum(prefix_form(op, Wt[:, m], y) for m in range(3))
     np.testing.assert_allclose(yk, want_y, rtol=1e-12, atol=1e-12)
     # no earlier components: nothing to deflate
     np.testing.assert_array_equal(oracle.deflate(op, Cm, np.zeros((D, 0))), Cm)
+
+
+@pytest.mark.parametrize("op", ["min1", "min2"])
+def test_min_deflation_of_equal_magnitudes_is_the_projection(op):
+    """A component of equal magnitudes (min2: equal signs too) gives, at unit
+    l1 norm, the outer product u u^T exactly, so the deflation of Alg. 2
+    step 6 is the projection deflation of §1 for it."""
+    r = datagen.rng(23)
+    D = 16
+    s = np.where(r.random(D) < 0.5, -1.0, 1.0) if op == "min1" else np.ones(D)
+    u = s / np.sqrt(D)
+    Cm = oracle.mincov(op, r.standard_normal((D, 40)), 40.0)
+    np.testing.assert_allclose(oracle.deflate(op, Cm, u[:, None]),
+                               Cm - np.outer(u, u) @ Cm, rtol=1e-13, atol=1e-13)
+    y = r.standard_normal(D)
+    np.testing.assert_allclose(oracle.deflate_vec(op, y, u[:, None]), y - u * (u @ y),
+                               rtol=1e-13, atol=1e-13)
+
+
+def test_min1_pca_components_follow_the_spikes():
+    """Under the unit-l1 outer products, min1 PCA with deflation finds the
+    spiked directions one after another (at unit l2 norm every component
+    after the first falls back onto the first spike)."""
+    D, N = 96, 6000
+    X = datagen.spiked_pca_data(D, N, seed=24, spikes=(60.0, 40.0, 25.0),
+                                outlier_frac=0.0).astype(np.float64)
+    r = datagen.rng(24)
+    U, _ = np.linalg.qr(r.standard_normal((D, 3)))
+    W0 = datagen.rng(25).uniform(-1, 1, size=(D, 3))
+    st, P, _ = oracle.pca_topk("mincov", "min1", X, 3, 60, float(N), W0)
+    assert st == oracle.OK
+    ov = np.abs(U.T @ P)
+    assert list(ov.argmax(axis=0)) == [0, 1, 2]
+    assert ov.max(axis=0).min() > 0.8
 
 
 def test_dot_deflation_is_projection_and_exposes_second_eigenvector():
@@ -350,6 +386,73 @@ def test_pca_dot_mincov_recovers_eigenvectors():
     st, P2, _ = oracle.pca_topk("pair", "dot", X, 3, 400, float(N), W0)
     for c in range(3):
         assert abs(P2[:, c] @ P[:, c]) > 1 - 1e-8
+
+
+# ------------------------------------------------- reconstruction (Alg. 2)
+
+def test_reconstruct_dot_is_the_orthogonal_projection():
+    r = datagen.rng(26)
+    D, N, k = 40, 6, 3
+    W, _ = np.linalg.qr(r.standard_normal((D, k)))
+    V = r.standard_normal((D, N))
+    m = r.standard_normal(D)
+    want = m[:, None] + W @ (W.T @ (V - m[:, None]))
+    np.testing.assert_allclose(oracle.reconstruct("dot", W, V, m), want, rtol=1e-12,
+                               atol=1e-12)
+    # a vector in the span comes back unchanged
+    V2 = m[:, None] + W @ r.standard_normal((k, N))
+    np.testing.assert_allclose(oracle.reconstruct("dot", W, V2, m), V2, rtol=1e-12,
+                               atol=1e-12)
+
+
+def test_reconstruct_min1_of_equal_magnitude_components_is_a_projection():
+    """Hadamard columns (equal magnitudes, orthogonal): each outer product at
+    unit l1 norm is u u^T, so step 8 projects onto their span."""
+    from scipy.linalg import hadamard
+    r = datagen.rng(27)
+    D = 16
+    H = hadamard(D).astype(np.float64)[:, [1, 4, 7]] * r.uniform(0.5, 2.0, 3)
+    U = H / np.linalg.norm(H, axis=0)
+    V = r.standard_normal((D, 5))
+    m = r.standard_normal(D)
+    want = m[:, None] + U @ (U.T @ (V - m[:, None]))
+    np.testing.assert_allclose(oracle.reconstruct("min1", H, V, m), want, rtol=1e-12,
+                               atol=1e-12)
+
+
+@pytest.mark.parametrize("op", MAVPS)
+def test_reconstruct_matches_prefix_form(op):
+    r = datagen.rng(28)
+    D, N = 30, 4
+    W = r.standard_normal((D, 2))
+    V = r.uniform(0, 1, (D, N))
+    m = V.mean(axis=1)
+    Wt = W / np.abs(W).sum(axis=0)
+    want = np.stack([m + sum(prefix_form(op, Wt[:, c], V[:, i] - m) for c in range(2))
+                     for i in range(N)], axis=1)
+    np.testing.assert_allclose(oracle.reconstruct(op, W, V, m), want, rtol=1e-12,
+                               atol=1e-12)
+
+
+def test_image_reconstruct_dot_full_rank_returns_the_images():
+    """With k = N - 1 converged RPI components the centred images lie in
+    their span, so step 8 returns every image (and m is the plain mean)."""
+    r = datagen.rng(29)
+    N, P = 4, 48
+    base = r.uniform(0.2, 0.8, P)
+    imgs = base + 0.3 * r.standard_normal((N, P)) * np.array([[3.0], [2.0], [1.2], [0.5]])
+    W0 = r.uniform(-1, 1, (P, N - 1))
+    st, W, R, its = oracle.image_reconstruct("dot", imgs, N - 1, 3000, W0, tol=1e-15)
+    assert st == oracle.OK
+    np.testing.assert_allclose(R, imgs, rtol=0, atol=1e-8)
+    np.testing.assert_allclose(W.T @ W, np.eye(N - 1), atol=1e-8)
+
+
+def test_image_reconstruct_of_identical_images_has_nothing_to_find():
+    # dyadic pixels and N = 4: the mean is exact, so V - m is exactly zero
+    imgs = np.tile(datagen.rng(30).integers(0, 9, 20) / 8.0, (4, 1))
+    st, _, R, _ = oracle.image_reconstruct("min2", imgs, 1, 10, np.ones((20, 1)))
+    assert st == oracle.EZERONORM and R is None
 
 
 # ------------------------------------------------------------ pair step
