@@ -235,15 +235,53 @@ mapi_status mapi_minibatch_momentum(mapi_ctx* ctx, const float* X, int N, int D,
 mapi_status mapi_mincov(mapi_ctx* ctx, const mapi_mat* X, mapi_op op,
                         double denom, float* C_out);
 
+/*
+ * Outer-product projection, Alg. 2 step 8 (and the operator of step 6):
+ * out_r = (W (+) W^T) in_r + add for `rows` input rows, with
+ * (W (+) W^T)_pq = sum_c term(wt_pc, wt_qc) (the matrix extension of the
+ * operator) and an ordinary product with in_r.  wt_c is column c of W at the
+ * unit norm of its iteration: W_c / ||W_c||_1 for MIN1 / MIN2 (Eq. (8)), W_c
+ * as given for DOT (then the product is W W^T in_r).  The D x D matrix is
+ * never formed: each component is ranked by |wt| once and every row takes
+ * two prefix sums over that order.
+ *   W: device D x k column-major (leading dimension ldw >= D), k in 1..64.
+ *   in, out: device rows x D row-major (ld_in, ld_out >= D); add: device D
+ *   or NULL.  1 <= D <= 16384.
+ * Errors: MAPI_EINVAL, MAPI_ECUDA.  Asynchronous on the context stream.
+ */
+mapi_status mapi_mavp_project(mapi_ctx* ctx, mapi_op op, const float* W, int64_t ldw, int D,
+                              int k, const float* in, int64_t ld_in, int rows, const float* add,
+                              float* out, int64_t ld_out);
+
+/*
+ * Image reconstruction by MAPI, Alg. 2 end to end.  images: device N x P
+ * row-major FP32, row i the pixels of image i (steps 1-2: v_i, V = [v_1 ..
+ * v_N]).  Step 3: m = the mean image, V - m.  Step 4: C = (V - m) (+)
+ * (V - m)^T / (N - 1) (P x P).  Steps 5-6: k components by MAPI (op MIN1 or
+ * MIN2; DOT gives the RPI baseline), each on C_c = C - sum_{m<c} P_m C, for
+ * iters steps (or until delta < tol_l1), ended at unit l2 norm.  Step 8, for
+ * every image: recon_i = (W (+) W^T)(v_i - m) + m as in mapi_mavp_project.
+ *   w0: device P x k column-major raw start vectors.  W_out: device P x k
+ *   column-major, the components.  recon_out: device N x P row-major.
+ *   iters_done: host k ints (may be NULL).  N >= 2, 1 <= P <= 16384,
+ *   1 <= k <= min(P, 64).
+ * Errors: MAPI_EINVAL, MAPI_EZERONORM / MAPI_ENONFINITE (a component; then
+ * recon_out is not written), MAPI_ENOMEM, MAPI_ECUDA.  Synchronous.
+ */
+mapi_status mapi_image_reconstruct(mapi_ctx* ctx, const float* images, int N, int P, int k,
+                                   mapi_op op, int iters, double tol_l1, const float* w0,
+                                   float* W_out, float* recon_out, int* iters_done);
+
 #define MAPI_PCA_MINCOV 0 /* Alg. 2: C = X (+) X^T / denom, deflate, MAPI */
 #define MAPI_PCA_PAIR 1   /* matrix-free: t = X^T (+) w, y = X (+) t / denom */
 
 /*
  * Top-k principal vectors by MAPI (Alg. 2 steps 4-7, k components).
  *   MINCOV: C = (1/cov_denom) X (+) X^T once; component c runs Alg. 1 on
- *     C_c = (I - sum_{m<c} P_m) C, P_m = w_m (+) w_m^T built from the earlier
- *     l2-normalised components, the product P_m C being ordinary (Alg. 2
- *     step 6 with the sum form that follows Eq. (2)).
+ *     C_c = (I - sum_{m<c} P_m) C, P_m = wt_m (+) wt_m^T built from the
+ *     earlier components at the unit norm of their iteration (l1 for MIN1 /
+ *     MIN2, l2 for DOT), the product P_m C being ordinary (Alg. 2 step 6 with
+ *     the sum form that follows Eq. (2)); k > 1 needs D <= 16384.
  *   PAIR: component c iterates y = X (+) (X^T (+) w) / cov_denom on X
  *     directly (t_n = x_n^T (+) w for every sample n, then y_d = sum_n
  *     X_dn (+) t_n / cov_denom), deflates y <- y - sum_{m<c} P_m y, and
@@ -253,8 +291,9 @@ mapi_status mapi_mincov(mapi_ctx* ctx, const mapi_mat* X, mapi_op op,
  *   w0: device, D x k column-major raw start vectors (each scaled to unit l2
  *   norm first).  P_out: device, D x k column-major.  iters_done: host, k
  *   ints (may be NULL).  tol_l1 <= 0 runs exactly iters_per_vec steps.
- * Errors: MAPI_EINVAL (k outside 1..min(D, 64), op), MAPI_EZERONORM,
- * MAPI_ENOMEM, MAPI_ECUDA.  Synchronous.
+ * Errors: MAPI_EINVAL (k outside 1..min(D, 64), op), MAPI_ENOTSUP (MINCOV
+ * with k > 1 and D > 16384), MAPI_EZERONORM, MAPI_ENOMEM, MAPI_ECUDA.
+ * Synchronous.
  */
 mapi_status mapi_pca_topk(mapi_ctx* ctx, const mapi_mat* X, int k, int mode,
                           mapi_op op, int iters_per_vec, double tol_l1,

@@ -26,7 +26,7 @@ __all__ = [
     "mapi_get_stats", "mapi_iterate_noalloc", "mapi_iterate_batched",
     "mapi_autotune_batched", "mapi_submit", "mapi_poll", "mapi_cancel",
     "mapi_pagerank_sparse", "mapi_iterate_switch", "mapi_minibatch_momentum",
-    "KERNEL_CLASSES",
+    "mapi_mavp_project", "mapi_image_reconstruct", "KERNEL_CLASSES",
     "OP", "ST", "FLAG_FINAL_L2", "FLAG_RAW_START", "SCALE_AUTO",
     "PCA_MINCOV", "PCA_PAIR", "STATUS",
 ]
@@ -112,6 +112,8 @@ def load(path: str | None = None):
         "mapi_mincov": [p_, p_, i, d, p_],
         "mapi_iterate_switch": [p_, p_, i, p_, i, d, i, d, u, p_, p_, p_],
         "mapi_minibatch_momentum": [p_, p_, i, i, p_, i, i, d, i, p_, u, p_],
+        "mapi_mavp_project": [p_, i, p_, i64, i, i, p_, i64, i, p_, p_, i64],
+        "mapi_image_reconstruct": [p_, p_, i, i, i, i, i, d, p_, p_, p_, p_],
         "mapi_pca_topk": [p_, p_, i, i, i, i, d, d, p_, p_, p_],
         "mapi_google_matrix": [p_, p_, p_, i, d, i, C.POINTER(p_)],
         "mapi_pagerank": [p_, p_, p_, i, d, i, i, p_, i, d, p_, p_, p_],
@@ -301,6 +303,45 @@ def mapi_minibatch_momentum(ctx, X, batch, beta: float, op, w0, flags: int = 0,
                                         C.c_void_p(_dptr(w_out)))
     _check(st, "mapi_minibatch_momentum", ctx, partial=w_out)
     return w_out
+
+
+def mapi_mavp_project(ctx, op, W, rows_in, add=None, out=None):
+    """out_r = (W (+) W^T) in_r + add (Alg. 2 step 8).  W: torch CUDA float32
+    (k, D) (row c is component c, i.e. D x k column-major); rows_in: (rows, D);
+    add: (D,) or None.  Returns out (rows, D)."""
+    torch = _torch()
+    W = W.contiguous()
+    rows_in = rows_in.contiguous()
+    k, D = W.shape
+    rows = rows_in.shape[0]
+    if out is None:
+        out = torch.empty((rows, D), dtype=torch.float32, device=rows_in.device)
+    opi = OP[op] if isinstance(op, str) else int(op)
+    addp = C.c_void_p(_dptr(add.contiguous())) if add is not None else None
+    _check(load().mapi_mavp_project(ctx, opi, C.c_void_p(_dptr(W)), int(D), int(D), int(k),
+                                    C.c_void_p(_dptr(rows_in)), int(D), int(rows), addp,
+                                    C.c_void_p(_dptr(out)), int(D)),
+           "mapi_mavp_project", ctx)
+    return out
+
+
+def mapi_image_reconstruct(ctx, images, k: int, op, iters: int, w0, tol_l1: float = 0.0):
+    """Alg. 2 on N images of P pixels (images: torch CUDA float32 (N, P));
+    w0: (k, P) raw start vectors.  Returns (W (k, P), recon (N, P), iters)."""
+    torch = _torch()
+    images = images.contiguous()
+    N, P = images.shape
+    W = torch.empty((k, P), dtype=torch.float32, device=images.device)
+    R = torch.empty((N, P), dtype=torch.float32, device=images.device)
+    it = (C.c_int * k)()
+    opi = OP[op] if isinstance(op, str) else int(op)
+    st = load().mapi_image_reconstruct(ctx, C.c_void_p(_dptr(images)), int(N), int(P), int(k),
+                                       opi, int(iters), float(tol_l1),
+                                       C.c_void_p(_dptr(w0.contiguous())), C.c_void_p(_dptr(W)),
+                                       C.c_void_p(_dptr(R)), it)
+    res = (W, R, list(it))
+    _check(st, "mapi_image_reconstruct", ctx, partial=res)
+    return res
 
 
 def mapi_mincov(ctx, X, op, denom: float, C_out=None):

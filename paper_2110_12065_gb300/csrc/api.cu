@@ -172,6 +172,10 @@ struct DeviceGuard {
   }
 };
 
+}  // namespace
+
+namespace mapi {
+
 mapi_status free_matrix(mapi_ctx* ctx, mapi_mat* m) {
   // graphs captured for this matrix can never be replayed again
   for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
@@ -222,6 +226,10 @@ mapi_status alloc_matrix(mapi_ctx* ctx, int rows, int cols, mapi_storage st,
   *out = m;
   return MAPI_OK;
 }
+
+}  // namespace mapi
+
+namespace {
 
 bool valid_matrix(mapi_ctx* ctx, const mapi_mat* m) {
   return m && ctx && ctx->mats.count(const_cast<mapi_mat*>(m));
@@ -378,7 +386,7 @@ mapi_status mapi_destroy(mapi_ctx* ctx) {
   for (auto* m : ms) free_matrix(ctx, m);
   for (DevBuf* b : {&ctx->ypart, &ctx->wbuf0, &ctx->wbuf1, &ctx->ctl, &ctx->aux, &ctx->mcpart,
                     &ctx->pca_c0, &ctx->pca_c1, &ctx->pca_q, &ctx->pca_defl, &ctx->batch,
-                    &ctx->hyb})
+                    &ctx->hyb, &ctx->outer, &ctx->img})
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);

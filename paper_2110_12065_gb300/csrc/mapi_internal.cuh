@@ -118,6 +118,9 @@ struct mapi_ctx {
   int* rec_host = nullptr;                 // pinned: per-component steps and statuses
   DevBuf batch;                            // batched solves: instance table and results
   DevBuf hyb;                              // MAPI -> RPI switch: the handed-over iterate
+  DevBuf outer;                            // ranked components of an outer-product apply
+  DevBuf img;                              // image reconstruction: centred images, mean
+  mapi_mat* img_X = nullptr;               // image reconstruction: packed centred images
   int batch_rows_per_warp[2][2] = {{2, 2}, {2, 2}};  // [F32, BF16][1, 4 vectors], autotuned
   mapi::IterCtl* ctl_host = nullptr;  // pinned mirror of the control block
 
@@ -179,6 +182,11 @@ void finish_graph(mapi_ctx* ctx, GraphEntry* g);
 // Grow a scratch buffer (drops cached graphs when an address changes).
 mapi_status ensure(mapi_ctx* ctx, DevBuf& b, size_t bytes);
 
+// Packed matrices owned by the context (api.cu): an uninitialised rows x cols
+// matrix of storage st, and its release.
+mapi_status alloc_matrix(mapi_ctx* ctx, int rows, int cols, mapi_storage st, mapi_mat** out);
+mapi_status free_matrix(mapi_ctx* ctx, mapi_mat* m);
+
 // --------------------------------------------------------- kernel launchers
 // Iteration launch parameters chosen per shape (see tune.cu).
 struct GemvPlan {
@@ -223,11 +231,38 @@ mapi_status launch_finish(mapi_ctx* ctx, cudaStream_t s, const float* wb0, const
 mapi_status launch_mincov_raw(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, float denom,
                               float* C, int64_t ldc, cudaStream_t s);
 size_t mincov_scratch_bytes(const mapi_ctx* ctx, const mapi_mat* X);
-// C_c = C - Q C with Q = sum_{m<c} P_m (+) P_m^T (columns of P, ldp apart);
-// C, Q and C_c are D x D row-major with leading dimension ld.
+
+// Outer products w (+) w^T of Alg. 2 (outer.cu).  A component is ranked once
+// into a slot: wt = the component at the unit norm of its iteration (l1 for
+// MIN1 / MIN2, as kept for DOT), perm / csort = the order of |wt|, ubi[i] =
+// the last sorted position whose |wt| is <= |wt_i|.  A scratch of k slots
+// holds 4 arrays of k x stride entries (wt, perm, csort, ubi).
+constexpr int kOuterMaxD = 16384;  // order of an applied outer product
+constexpr int kOuterMaxK = 64;     // components in one apply
+struct OuterSlot {
+  float* wt;
+  int* perm;
+  float* csort;
+  int* ubi;
+};
+inline int64_t outer_stride(int D) { return ((int64_t)D + 3) / 4 * 4; }
+OuterSlot outer_slot(void* base, int k, int64_t stride, int m);
+size_t outer_scratch_bytes(int k, int D);
+// Shared-memory limits of the outer-product kernels (call before capture).
+mapi_status outer_prepare(mapi_ctx* ctx);
+mapi_status launch_outer_prep(mapi_ctx* ctx, mapi_op op, const float* w, int D, OuterSlot slot,
+                              cudaStream_t s);
+// out_r = sum_{m<nprev} P_m in_r (+ add) for `rows` rows (slots first...).
+mapi_status launch_outer_apply(mapi_ctx* ctx, mapi_op op, int D, int nprev, OuterSlot first,
+                               int64_t stride, const float* in, int64_t ld_in, int rows,
+                               const float* add, float* out, int64_t ld_out, cudaStream_t s);
+// Alg. 2 step 6: C_c = C - sum_{m<c} P_m C for symmetric C (D x D, leading
+// dimension ld).  Ranks component c - 1 (column c - 1 of P) into slot c - 1
+// of `rank` (slots 0 .. c - 2 hold the earlier ones from the previous
+// calls), forms T = rows of (sum_m P_m C)^T, then C_c = C - T^T.
 mapi_status launch_deflate_mincov(mapi_ctx* ctx, mapi_op op, const float* P, int64_t ldp, int c,
-                                  int D, const float* C, int64_t ld, float* Q, float* Cc,
-                                  cudaStream_t s);
+                                  int D, const float* C, int64_t ld, float* T, void* rank,
+                                  int kslots, int64_t stride, float* Cc, cudaStream_t s);
 
 // Batched solves (batched.cu): one instance as the kernel sees it.
 struct BatchDev {

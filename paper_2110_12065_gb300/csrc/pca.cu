@@ -167,137 +167,25 @@ __global__ void k_mincov_reduce(const float* __restrict__ part, int ntiles, int 
 }
 
 // ======================================================================
-// Deflation operator Q = sum_{m<c} w_m (+) w_m^T (entry (i, j) =
-// sum_m term(w_m[i], w_m[j])), from the finished l2-normalised components.
-// ======================================================================
-template <int OP>
-__global__ void k_build_Q(const float* __restrict__ P, int64_t ldp, int c, int D,
-                          float* __restrict__ Q, int64_t ldq) {
-  const int64_t total = (int64_t)D * D;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / D), j = (int)(t % D);
-    float s = 0.f;
-    for (int m = 0; m < c; ++m) {
-      const float wi = P[(int64_t)m * ldp + i], wj = P[(int64_t)m * ldp + j];
-      s += (OP == MAPI_OP_DOT) ? wi * wj : Op<OP>::term(wi, Op<OP>::prep(wj), 0.f);
-    }
-    Q[(int64_t)i * ldq + j] = s;
-  }
-}
-
-// C_c = C - Q C (ordinary FP32 product), 64 x 64 tiles, 4 x 4 micro-tiles.
-__global__ void __launch_bounds__(256)
-    k_deflate_gemm(const float* __restrict__ Cm, const float* __restrict__ Q, int D,
-                   int64_t ld, float* __restrict__ Ck) {
-  __shared__ float Qs[16][65];
-  __shared__ float Cs[16][65];
-  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  float acc[4][4] = {};
-  for (int l0 = 0; l0 < D; l0 += 16) {
-    for (int e = threadIdx.x; e < 64 * 16; e += 256) {
-      const int r = e >> 4, l = e & 15;
-      Qs[l][r] = (i0 + r < D && l0 + l < D) ? Q[(int64_t)(i0 + r) * ld + l0 + l] : 0.f;
-      const int l2 = e >> 6, c2 = e & 63;
-      Cs[l2][c2] = (l0 + l2 < D && j0 + c2 < D) ? Cm[(int64_t)(l0 + l2) * ld + j0 + c2] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int l = 0; l < 16; ++l) {
-      float a[4], bb[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = Qs[l][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bb[j] = Cs[l][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = i0 + ty * 4 + i, c = j0 + tx * 4 + j;
-      if (r < D && c < D) Ck[(int64_t)r * ld + c] = Cm[(int64_t)r * ld + c] - acc[i][j];
-    }
-}
-
-// ======================================================================
-// Deflation of an iterate without forming Q.  For P = w (+) w^T with
-// c = |w|, s = sign(w) and z = s * y (min1):
+// Deflation of an iterate without forming the outer products.  For
+// P = wt (+) wt^T with c = |wt|, s = sign(wt) and z = s * y (min1):
 //   (P y)_i = s_i [ sum_{c_j <= c_i} c_j z_j + c_i sum_{c_j > c_i} z_j ],
-// which only needs w sorted by c: two prefix sums over the sorted order.
+// which only needs wt sorted by c: two prefix sums over the sorted order.
 // min2's outer product is half of (the min1 one + the same with every sign
-// +1); dot's is w (w . y).  k_defl_prep ranks one finished component once:
-// perm[p] = index at sorted position p, csort[p] = its c, ubi[i] = last
-// sorted position whose c is <= c_i (ties included).
+// +1); dot's is w (w . y).  wt is the component at unit l1 norm for min1 /
+// min2 (the unit of Eq. (8)'s iteration) and the kept unit-l2 component for
+// dot; launch_outer_prep ranks a finished component once: perm[p] = index
+// at sorted position p, csort[p] = its c, ubi[i] = last sorted position whose
+// c is <= c_i (ties included).
 // ======================================================================
 constexpr int kDeflMaxD = 1024;
-
-__global__ void __launch_bounds__(kDeflMaxD) k_defl_prep(const float* __restrict__ w, int D,
-                                                        int* __restrict__ perm,
-                                                        float* __restrict__ csort,
-                                                        int* __restrict__ ubi) {
-  __shared__ float c[kDeflMaxD];
-  for (int i = threadIdx.x; i < D; i += blockDim.x) c[i] = fabsf(w[i]);
-  __syncthreads();
-  for (int i = threadIdx.x; i < D; i += blockDim.x) {
-    const float ci = c[i];
-    int rank = 0, le = 0;
-    for (int j = 0; j < D; ++j) {
-      const float cj = c[j];
-      rank += (cj < ci) || (cj == ci && j < i);
-      le += (cj <= ci);
-    }
-    perm[rank] = i;
-    csort[rank] = ci;
-    ubi[i] = le - 1;
-  }
-}
-
-// In-place inclusive scan of x[0 .. 4*NT) in shared memory (fixed order).
-template <int NT>
-__device__ __forceinline__ void block_scan4(float* x, float* wtot) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  float v[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) v[k] = x[t * 4 + k];
-#pragma unroll
-  for (int k = 1; k < 4; ++k) v[k] += v[k - 1];
-  float incl = v[3];
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float n = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += n;
-  }
-  if (lane == 31) wtot[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    float wv = lane < NT / 32 ? wtot[lane] : 0.f;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const float n = __shfl_up_sync(0xffffffffu, wv, o);
-      if (lane >= o) wv += n;
-    }
-    if (lane < NT / 32) wtot[lane] = wv;  // inclusive over warps
-  }
-  __syncthreads();
-  const float off = (incl - v[3]) + (warp > 0 ? wtot[warp - 1] : 0.f);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) x[t * 4 + k] = off + v[k];
-  __syncthreads();
-}
 
 struct DeflArgs {
   int nprev;          // finished components to deflate (0: none)
   int op;             // MAPI_OP_MIN1 / MIN2 / DOT
-  const float* P;     // components, column m at P + m * ldp
+  const float* P;     // outer-product vectors wt, column m at P + m * ldp
   int64_t ldp;
-  const int* perm;    // [m][D_pad] per component (k_defl_prep)
+  const int* perm;    // [m][D_pad] per component (launch_outer_prep)
   const float* csort;
   const int* ubi;
   int64_t stride;     // elements between components in perm / csort / ubi
@@ -930,18 +818,6 @@ mapi_status launch_mincov_raw(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, floa
   return MAPI_OK;
 }
 
-static mapi_status launch_build_Q(mapi_ctx* ctx, mapi_op op, const float* P, int64_t ldp,
-                                  int c, int D, float* Q, int64_t ldq, cudaStream_t s) {
-  const int64_t total = (int64_t)D * D;
-  const int g = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->sm_count * 16);
-  if (op == MAPI_OP_MIN1) k_build_Q<MAPI_OP_MIN1><<<g, 256, 0, s>>>(P, ldp, c, D, Q, ldq);
-  else if (op == MAPI_OP_MIN2) k_build_Q<MAPI_OP_MIN2><<<g, 256, 0, s>>>(P, ldp, c, D, Q, ldq);
-  else k_build_Q<MAPI_OP_DOT><<<g, 256, 0, s>>>(P, ldp, c, D, Q, ldq);
-  MAPI_CUDA_TRY(ctx, cudaGetLastError());
-  count_launch(ctx);
-  return MAPI_OK;
-}
-
 struct PairLaunch {
   const void* fn = nullptr;
   int rw = 0;
@@ -1102,18 +978,6 @@ size_t mincov_scratch_bytes(const mapi_ctx* ctx, const mapi_mat* X) {
   return sizeof(float) * (size_t)nsplit * nt * kMcT * kMcT;
 }
 
-mapi_status launch_deflate_mincov(mapi_ctx* ctx, mapi_op op, const float* P, int64_t ldp, int c,
-                                  int D, const float* C, int64_t ld, float* Q, float* Cc,
-                                  cudaStream_t s) {
-  mapi_status st = launch_build_Q(ctx, op, P, ldp, c, D, Q, ld, s);
-  if (st != MAPI_OK) return st;
-  dim3 g((D + 63) / 64, (D + 63) / 64);
-  k_deflate_gemm<<<g, 256, 0, s>>>(C, Q, D, ld, Cc);
-  MAPI_CUDA_TRY(ctx, cudaGetLastError());
-  count_launch(ctx);
-  return MAPI_OK;
-}
-
 namespace {
 
 // Everything one PCA solve touches on the device, sized before capture.
@@ -1149,12 +1013,11 @@ mapi_status pca_enqueue(mapi_ctx* ctx, cudaStream_t s, const mapi_mat* X, const 
     for (int c = 0; c < k; ++c) {
       const mapi_mat* A = &p.Cm;
       if (c > 0) {
-        if ((st = launch_build_Q(ctx, p.op, P_out, D, c, D, p.Q, p.ldq, s)) != MAPI_OK) return st;
-        dim3 g((D + 63) / 64, (D + 63) / 64);
-        k_deflate_gemm<<<g, 256, 0, s>>>((const float*)p.Cm.data, p.Q, D, p.ldq,
-                                         (float*)p.Ck.data);
-        MAPI_CUDA_TRY(ctx, cudaGetLastError());
-        count_launch(ctx);
+        // Alg. 2 step 6: C_c = C - sum_{m<c} P_m C (p.Q holds the transposed product)
+        if ((st = launch_deflate_mincov(ctx, p.op, P_out, D, c, D, (const float*)p.Cm.data,
+                                        p.ldq, p.Q, p.defl, k, outer_stride(D),
+                                        (float*)p.Ck.data, s)) != MAPI_OK)
+          return st;
         A = &p.Ck;
       }
       if ((st = enqueue_solve(ctx, s, A, p.op, 1, w0 + (int64_t)c * D, D, p.iters, p.tol,
@@ -1171,24 +1034,22 @@ mapi_status pca_enqueue(mapi_ctx* ctx, cudaStream_t s, const mapi_mat* X, const 
   float* wb1 = (float*)ctx->wbuf1.p;
   IterCtl* ctl = (IterCtl*)ctx->ctl.p;
   const int norm_l2 = (p.op == MAPI_OP_DOT) ? 1 : 0;
-  int* perm = (int*)p.defl;
-  float* csort = (float*)((int*)p.defl + (size_t)k * p.D_pad);
-  int* ubi = (int*)p.defl + 2 * (size_t)k * p.D_pad;
+  const OuterSlot slot0 = outer_slot(p.defl, k, p.D_pad, 0);
   DeflArgs defl{};
   defl.op = p.op;
-  defl.P = P_out;
-  defl.ldp = D;
+  // dot deflates with the kept unit-l2 components, min1 / min2 with their
+  // unit-l1 copies (launch_outer_prep)
+  defl.P = p.op == MAPI_OP_DOT ? P_out : slot0.wt;
+  defl.ldp = p.op == MAPI_OP_DOT ? D : p.D_pad;
   defl.stride = p.D_pad;
-  defl.perm = perm;
-  defl.csort = csort;
-  defl.ubi = ubi;
+  defl.perm = slot0.perm;
+  defl.csort = slot0.csort;
+  defl.ubi = slot0.ubi;
   for (int c = 0; c < k; ++c) {
     if (c > 0 && p.op != MAPI_OP_DOT) {
-      const size_t o = (size_t)(c - 1) * p.D_pad;
-      k_defl_prep<<<1, kDeflMaxD, 0, s>>>(P_out + (int64_t)(c - 1) * D, D, perm + o, csort + o,
-                                         ubi + o);
-      MAPI_CUDA_TRY(ctx, cudaGetLastError());
-      count_launch(ctx);
+      if ((st = launch_outer_prep(ctx, p.op, P_out + (int64_t)(c - 1) * D, D,
+                                  outer_slot(p.defl, k, p.D_pad, c - 1), s)) != MAPI_OK)
+        return st;
     }
     defl.nprev = c;
     if ((st = launch_start_float(ctx, s, w0 + (int64_t)c * D, D, D, 1, wb0, wb1, p.wst, 0, ctl,
@@ -1242,7 +1103,13 @@ mapi_status run_pca(mapi_ctx* ctx, const mapi_mat* X, int k, int mode, mapi_op o
         (st = ensure(ctx, ctx->pca_c1, bytes)) != MAPI_OK ||
         (st = ensure(ctx, ctx->mcpart, mincov_scratch_bytes(ctx, X))) != MAPI_OK)
       return st;
-    if (k > 1 && (st = ensure(ctx, ctx->pca_q, sizeof(float) * p.D * p.ldq)) != MAPI_OK) return st;
+    if (k > 1) {
+      if (p.D > kOuterMaxD)
+        return fail(ctx, MAPI_ENOTSUP, "min-covariance deflation supports D <= 16384");
+      if ((st = ensure(ctx, ctx->pca_q, sizeof(float) * p.D * p.ldq)) != MAPI_OK ||
+          (st = ensure(ctx, ctx->pca_defl, outer_scratch_bytes(k, p.D))) != MAPI_OK)
+        return st;
+    }
     if ((st = prepare_solve(ctx, &p.Cm, 1)) != MAPI_OK) return st;
   } else {
     if ((st = plan_pair(ctx, X, op, &p.pl)) != MAPI_OK) return st;
@@ -1253,9 +1120,10 @@ mapi_status run_pca(mapi_ctx* ctx, const mapi_mat* X, int k, int mode, mapi_op o
         (st = ensure(ctx, ctx->ypart,
                      sizeof(float) * (size_t)p.pl.clusters * p.D_pad)) != MAPI_OK ||
         (st = ensure(ctx, ctx->ctl, sizeof(IterCtl))) != MAPI_OK ||
-        (st = ensure(ctx, ctx->pca_defl, sizeof(int) * 3 * (size_t)k * p.D_pad)) != MAPI_OK)
+        (st = ensure(ctx, ctx->pca_defl, sizeof(float) * 4 * (size_t)k * p.D_pad)) != MAPI_OK)
       return st;
   }
+  if ((st = outer_prepare(ctx)) != MAPI_OK) return st;
   // addresses are final now (ensure may have moved buffers and dropped graphs)
   p.rec = (int*)((char*)ctx->aux.p + 64);
   p.abort = p.rec + 128;

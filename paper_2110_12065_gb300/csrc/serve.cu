@@ -40,6 +40,7 @@ struct ServeReq {
   float* C = nullptr;   // PCA: C, C_c and Q, D x ldc each
   float* Cc = nullptr;
   float* Q = nullptr;
+  void* R = nullptr;    // PCA: ranked components of the deflation
   int64_t ldc = 0;
   float* P = nullptr;   // PCA components, D x k
   float* w0 = nullptr;  // start vectors
@@ -105,7 +106,7 @@ size_t request_bytes(const mapi_ctx* ctx, const mapi_request& r) {
     const size_t ldc = (size_t)(r.D + 3) / 4 * 4;
     return (size_t)r.D * r.N * 4 + packed_bytes(r.D, r.N, r.storage) +
            mincov_scratch_bytes(ctx, &x) + 3 * (size_t)((r.D + 63) / 64 * 64) * ldc * 4 +
-           (size_t)r.D * (2 * r.k + 2) * 4;
+           (size_t)r.D * (2 * r.k + 2) * 4 + outer_scratch_bytes(r.k, r.D);
   }
   const size_t nnz = (size_t)r.indptr[r.n];
   return (size_t)(r.n + 1 + nnz) * 4 + (size_t)r.n * ((r.n + 3) / 4 * 4) * 4 +
@@ -164,11 +165,12 @@ void release(Server* sv, ServeReq* q, bool in_builder) {
     if (q->G) sv->to_free.push_back(q->G);
     sv->bcv.notify_all();
   }
-  for (void* p : {(void*)q->C, (void*)q->Cc, (void*)q->Q, (void*)q->P, (void*)q->w0,
+  for (void* p : {(void*)q->C, (void*)q->Cc, (void*)q->Q, q->R, (void*)q->P, (void*)q->w0,
                   (void*)q->wb[0], (void*)q->wb[1]})
     dev_free(c, p);
   q->X = q->G = nullptr;
   q->C = q->Cc = q->Q = q->P = q->w0 = q->wb[0] = q->wb[1] = nullptr;
+  q->R = nullptr;
 }
 
 // Record the outcome and hand the request back to mapi_poll.
@@ -204,6 +206,7 @@ mapi_status build(Server* sv, ServeReq* q) {
       return s;
     if ((s = dev_alloc(c, &q->C, cb)) != MAPI_OK || (s = dev_alloc(c, &q->Cc, cb)) != MAPI_OK ||
         (s = dev_alloc(c, &q->Q, cb)) != MAPI_OK ||
+        (s = dev_alloc(c, &q->R, outer_scratch_bytes(r.k, D))) != MAPI_OK ||
         (s = dev_alloc(c, &q->P, sizeof(float) * (size_t)D * r.k)) != MAPI_OK ||
         (s = dev_alloc(c, &q->w0, sizeof(float) * (size_t)D * r.k)) != MAPI_OK ||
         (s = dev_alloc(c, &q->wb[0], sizeof(float) * D)) != MAPI_OK ||
@@ -279,9 +282,11 @@ mapi_status component_done(Server* sv, ServeReq* q, bool* all_done) {
     *all_done = true;
     return MAPI_OK;
   }
-  // Alg. 2 step 6: C_c = C - sum_{m<c} P_m (+) P_m^T C
-  mapi_status s = launch_deflate_mincov(c, r.op, q->P, D, q->comp, D, q->C, q->ldc, q->Q, q->Cc,
-                                        c->stream);
+  // Alg. 2 step 6: C_c = C - sum_{m<c} P_m C
+  mapi_status s = outer_prepare(c);
+  if (s == MAPI_OK)
+    s = launch_deflate_mincov(c, r.op, q->P, D, q->comp, D, q->C, q->ldc, q->Q, q->R, r.k,
+                              outer_stride(D), q->Cc, c->stream);
   if (s != MAPI_OK) return s;
   q->A = (const uint8_t*)q->Cc;
   q->view.data = q->Cc;
