@@ -420,8 +420,77 @@ def run_variants(M, ctx, torch, dev, X, W0d, peaks):
         "row_step_hbm_frac": round(gv["bytes"] / (gv["ms"] / 1e3) / 1e9 / hbm, 4)
         if gv["ms"] else None,
         "algorithmic_bytes_per_row_step": 16 * nnz + 8 * n}
+    out["image_reconstruct_128"] = run_image(M, ctx, torch, dev, hbm)
+    out["minibatch_momentum_1e6x10"] = run_minibatch(M, ctx, torch, dev)
     out["serve_mixed"] = run_serving(M, torch, dev)
     return out
+
+
+def psnr(a, b) -> float:
+    return float(10.0 * np.log10(1.0 / np.mean((np.asarray(a, np.float64) - b) ** 2)))
+
+
+def run_image(M, ctx, torch, dev, hbm):
+    """Alg. 2 on ten occluded 128 x 128 images (3 of 16 tiles noise): 2
+    components x 50 steps on the 16384 x 16384 min-covariance, every image
+    reconstructed; PSNR of the reconstructions against the clean image."""
+    import datagen
+    side, N, k, T = 128, 10, 2, 50
+    P = side * side
+    clean, imgs = datagen.occluded_images(side, N, grid=4, n_occ=3, seed=0)
+    dimg = torch.from_numpy(imgs.reshape(N, P)).to(dev)
+    W0 = torch.from_numpy(np.stack([datagen.start_vector(P, seed=50 + c)
+                                    for c in range(k)])).to(dev)
+    res = {"images": N, "pixels": P, "components": k, "steps": T,
+           "psnr_corrupted_mean": round(float(np.mean([psnr(im, clean) for im in imgs])), 2)}
+    for op in ("min2", "min1", "dot"):
+        run = lambda: M.mapi_image_reconstruct(ctx, dimg, k, op, T, W0)
+        ms = timed(torch, run, 2)
+        _, R, its = run()
+        R = R.cpu().numpy().reshape(N, side, side)
+        res[op] = {"ms_per_reconstruction": round(ms, 3), "iters": its,
+                   "psnr_mean": round(float(np.mean([psnr(r, clean) for r in R])), 2)}
+    # the parts: Eq. (5) build and the steps (instrumented), and one step-6
+    # deflation's row pass over the 1 GiB C (read C rows, write the product)
+    M.mapi_profile(ctx, True)
+    M.mapi_image_reconstruct(ctx, dimg, k, "min2", T, W0)
+    torch.cuda.synchronize()
+    M.mapi_get_stats(ctx, reset=True)
+    M.mapi_image_reconstruct(ctx, dimg, k, "min2", T, W0)
+    torch.cuda.synchronize()
+    st = M.mapi_get_stats(ctx, reset=True)
+    M.mapi_profile(ctx, False)
+    mc, gv = st["mincov"], st["gemv"]
+    gbs = gv["bytes"] / (gv["ms"] / 1e3) / 1e9 if gv["ms"] else 0.0
+    res["build_ms"] = round(mc["ms"] / max(1, mc["launches"]), 3)
+    res["step_us"] = round(gv["ms"] / max(1, gv["launches"]) * 1e3, 2)
+    res["step_gbs"] = round(gbs, 1)
+    res["step_hbm_frac"] = round(gbs / hbm, 4)
+    Cbig = torch.rand((P, P), device=dev)
+    out = torch.empty_like(Cbig)
+    ms = timed(torch, lambda: M.mapi_mavp_project(ctx, "min2", W0, Cbig, out=out), 3)
+    res["deflation_row_pass_ms"] = round(ms, 3)
+    res["deflation_row_pass_gbs"] = round(2.0 * P * P * 4 / (ms / 1e3) / 1e9, 1)
+    del Cbig, out
+    return res
+
+
+def run_minibatch(M, ctx, torch, dev):
+    """Alg. 3 on the 10^6 x 10 synthetic set: 100 steps of 1000 draws."""
+    import datagen
+    Nn, Dd, T, s = 10 ** 6, 10, 100, 1000
+    X = datagen.stochastic_pca_data(Nn, Dd, seed=0)
+    b = datagen.minibatches(Nn, T, s, seed=1)
+    Xd, bd = torch.from_numpy(X).to(dev), torch.from_numpy(b).to(dev)
+    w0 = torch.from_numpy(datagen.start_vector(Dd, seed=2)).to(dev)
+    res = {"N": Nn, "D": Dd, "steps": T, "batch": s, "beta": 0.2025}
+    for op in ("min1", "dot"):
+        ms = timed(torch, lambda: M.mapi_minibatch_momentum(ctx, Xd, bd, 0.2025, op, w0,
+                                                           M.FLAG_FINAL_L2), 5)
+        terms = float(T) * Dd * Dd * s
+        res[op] = {"ms_per_solve": round(ms, 3), "steps_per_s": round(T / (ms / 1e3), 1),
+                   "terms_per_s": round(terms / (ms / 1e3), 1)}
+    return res
 
 
 def serving_workload(count: int, seed: int = 0):
@@ -665,6 +734,21 @@ def run_case(case: str):
         _, it, _ = M.mapi_pagerank(ctx, torch.from_numpy(ip).cuda(), torch.from_numpy(ix).cuda(),
                                    n, w0, 6, storage=st)
         out = f"{case}: n={n}, {it} steps"
+    elif case == "image":
+        side, Nn, k = 128, 10, 2
+        _, imgs = datagen.occluded_images(side, Nn, grid=4, n_occ=3, seed=0)
+        W0 = torch.from_numpy(np.stack([datagen.start_vector(side * side, seed=50 + c)
+                                        for c in range(k)])).cuda()
+        _, _, its = M.mapi_image_reconstruct(ctx, torch.from_numpy(imgs.reshape(Nn, -1)).cuda(),
+                                             k, "min2", 6, W0)
+        out = f"{case}: {Nn} images of {side}x{side}, {k} components, iters {its}"
+    elif case == "minibatch":
+        X = datagen.stochastic_pca_data(10 ** 6, 10, seed=0)
+        b = datagen.minibatches(10 ** 6, 100, 1000, seed=1)
+        w0 = torch.from_numpy(datagen.start_vector(10, seed=2)).cuda()
+        M.mapi_minibatch_momentum(ctx, torch.from_numpy(X).cuda(), torch.from_numpy(b).cuda(),
+                                  0.2025, "min1", w0)
+        out = f"{case}: 10^6 x 10, 100 steps of 1000"
     elif case == "serve":
         import torch
         out = json.dumps(run_serving(M, torch, "cuda"))
@@ -698,7 +782,8 @@ def main():
     ap.add_argument("--case", default=None,
                     help="run one short solve of a workload for a profiler and exit: "
                          "pair-f32, pair-bf16, mincov-f32, mincov-bf16, pagerank-f32, "
-                         "pagerank-bf16, pagerank-fp8, pagerank-i16, pagerank-sparse, batched-f32, serve")
+                         "pagerank-bf16, pagerank-fp8, pagerank-i16, pagerank-sparse, batched-f32, serve, "
+                         "image, minibatch")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)

@@ -234,15 +234,16 @@ size_t mincov_scratch_bytes(const mapi_ctx* ctx, const mapi_mat* X);
 
 // Outer products w (+) w^T of Alg. 2 (outer.cu).  A component is ranked once
 // into a slot: wt = the component at the unit norm of its iteration (l1 for
-// MIN1 / MIN2, as kept for DOT), perm / csort = the order of |wt|, ubi[i] =
-// the last sorted position whose |wt| is <= |wt_i|.  A scratch of k slots
-// holds 4 arrays of k x stride entries (wt, perm, csort, ubi).
+// MIN1 / MIN2, as kept for DOT), perm = the order of |wt|, wsort[p] =
+// wt[perm[p]], ubi[i] = the last sorted position whose |wt| is <= |wt_i|.  A
+// scratch of k slots holds 4 arrays of k x stride entries (wt, perm, wsort,
+// ubi).
 constexpr int kOuterMaxD = 16384;  // order of an applied outer product
 constexpr int kOuterMaxK = 64;     // components in one apply
 struct OuterSlot {
   float* wt;
   int* perm;
-  float* csort;
+  float* wsort;
   int* ubi;
 };
 inline int64_t outer_stride(int D) { return ((int64_t)D + 3) / 4 * 4; }

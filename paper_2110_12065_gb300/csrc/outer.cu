@@ -12,7 +12,7 @@
 //   (P y)_i = s_i [ sum_{c_j <= c_i} c_j z_j + c_i sum_{c_j > c_i} z_j ],
 // two prefix sums over the order of c; MIN2's outer product is half of MIN1's
 // plus the same with every sign +1; DOT's is wt (wt . y).  k_outer_prep ranks
-// a component once (perm, csort, ubi), k_outer_apply runs the prefix sums
+// a component once (perm, wsort, ubi), k_outer_apply runs the prefix sums
 // for one input row per CTA with the row, and the two prefix arrays, in
 // shared memory.
 #include <algorithm>
@@ -23,86 +23,98 @@ namespace mapi {
 
 namespace {
 
-constexpr int kPrepThreads = 256;
+constexpr int kPrepThreads = 1024;
 constexpr int kApplyThreads = 1024;
 
-// Ranks component w (length D) into one slot: wt = the scaled component,
-// perm[p] = index at sorted position p (ties by index), csort[p] = its |wt|,
-// ubi[i] = the last sorted position whose |wt| is <= |wt_i|.  Every CTA
-// forms the same scale and magnitudes (fixed order); CTA b ranks indices
-// [256 b, 256 b + 256).  DOT only needs wt.
+// Ranks component w (length D) into one slot, one CTA: wt = the scaled
+// component, perm[p] = index at sorted position p (order of |wt|, ties by
+// index), wsort[p] = wt[perm[p]], ubi[i] = the last sorted position whose
+// |wt| is <= |wt_i|.  The keys (|wt| bits, index) are sorted by a bitonic
+// network in shared memory (Dp = D rounded up to a power of two, padded with
+// the largest key).  DOT only needs wt.
 __global__ void __launch_bounds__(kPrepThreads)
-    k_outer_prep(const float* __restrict__ w, int D, int op, OuterSlot r) {
-  extern __shared__ float cs[];  // D magnitudes
+    k_outer_prep(const float* __restrict__ w, int D, int Dp, int op, OuterSlot r) {
+  extern __shared__ unsigned long long keys[];
   __shared__ float red[33];
-  float L = 1.f;
-  if (op != MAPI_OP_DOT) {
-    Kahan k;
-    for (int i = threadIdx.x; i < D; i += kPrepThreads) k.add(fabsf(w[i]));
-    L = block_sum<kPrepThreads>(k.value(), red);
-    if (!(L > 0.f)) L = 1.f;
-  }
-  const int i = blockIdx.x * kPrepThreads + threadIdx.x;
+  const int t = threadIdx.x;
   if (op == MAPI_OP_DOT) {
-    if (i < D) r.wt[i] = w[i];
+    for (int i = t; i < D; i += kPrepThreads) r.wt[i] = w[i];
     return;
   }
-  for (int j = threadIdx.x; j < D; j += kPrepThreads) cs[j] = fabsf(w[j] / L);
-  __syncthreads();
-  if (i >= D) return;
-  const float wi = w[i] / L;
-  const float ci = cs[i];
-  int below = 0, le = 0, tie_before = 0;
-  int j = 0;
-  for (; j + 4 <= D; j += 4) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float cj = cs[j + u];
-      below += cj < ci;
-      le += cj <= ci;
-      tie_before += (cj == ci) & (j + u < i);
+  Kahan k;
+  for (int i = t; i < D; i += kPrepThreads) k.add(fabsf(w[i]));
+  float L = block_sum<kPrepThreads>(k.value(), red);
+  if (!(L > 0.f)) L = 1.f;
+  for (int j = t; j < Dp; j += kPrepThreads) {
+    unsigned long long key = ~0ull;
+    if (j < D) {
+      const float wj = w[j] / L;
+      r.wt[j] = wj;
+      key = ((unsigned long long)__float_as_uint(fabsf(wj)) << 32) | (unsigned)j;
     }
+    keys[j] = key;
   }
-  for (; j < D; ++j) {
-    const float cj = cs[j];
-    below += cj < ci;
-    le += cj <= ci;
-    tie_before += (cj == ci) & (j < i);
+  __syncthreads();
+  for (int size = 2; size <= Dp; size <<= 1)
+    for (int lh = __ffs(size) - 2; lh >= 0; --lh) {
+      const int half = 1 << lh;
+      for (int x = t; x < Dp / 2; x += kPrepThreads) {
+        const int i = ((x >> lh) << (lh + 1)) | (x & (half - 1));
+        const int l = i + half;
+        const bool up = (i & size) == 0;
+        const unsigned long long ki = keys[i], kl = keys[l];
+        if ((ki > kl) == up) {
+          keys[i] = kl;
+          keys[l] = ki;
+        }
+      }
+      __syncthreads();
+    }
+  for (int p = t; p < D; p += kPrepThreads) {
+    const unsigned long long key = keys[p];
+    const int i = (int)(key & 0xffffffffu);
+    const unsigned cb = (unsigned)(key >> 32);
+    // last position whose magnitude bits are <= cb
+    int lo = p, hi = Dp - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if ((unsigned)(keys[mid] >> 32) <= cb) lo = mid;
+      else hi = mid - 1;
+    }
+    r.perm[p] = i;
+    r.wsort[p] = w[i] / L;
+    r.ubi[i] = lo;
   }
-  const int rank = below + tie_before;
-  r.perm[rank] = i;
-  r.csort[rank] = ci;
-  r.ubi[i] = le - 1;
-  r.wt[i] = wi;
 }
 
-// Inclusive block scan of a[E], b[E] held by each thread over consecutive
-// positions (thread t owns [t E, t E + E)); fixed order.
+// Inclusive scan of two value sets over positions p = e * 1024 + t (thread
+// t holds a[e], b[e] for e < E): a warp scan per e, the warp totals scanned
+// by warp e, then the totals of the E blocks of 1024 added in order.
+// tot: 2 x E x 32 floats of shared memory.
 template <int E>
-__device__ __forceinline__ void block_scan2(float (&a)[E], float (&b)[E], float* wa, float* wb) {
+__device__ __forceinline__ void block_scan_strided(float (&a)[E], float (&b)[E], float* tot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* ta = tot;
+  float* tb = tot + E * 32;
 #pragma unroll
-  for (int e = 1; e < E; ++e) {
-    a[e] += a[e - 1];
-    b[e] += b[e - 1];
-  }
-  float ta = a[E - 1], tb = b[E - 1];
+  for (int e = 0; e < E; ++e) {
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float na = __shfl_up_sync(0xffffffffu, ta, o);
-    const float nb = __shfl_up_sync(0xffffffffu, tb, o);
-    if (lane >= o) {
-      ta += na;
-      tb += nb;
+    for (int o = 1; o < 32; o <<= 1) {
+      const float na = __shfl_up_sync(0xffffffffu, a[e], o);
+      const float nb = __shfl_up_sync(0xffffffffu, b[e], o);
+      if (lane >= o) {
+        a[e] += na;
+        b[e] += nb;
+      }
+    }
+    if (lane == 31) {
+      ta[e * 32 + warp] = a[e];
+      tb[e * 32 + warp] = b[e];
     }
   }
-  if (lane == 31) {
-    wa[warp] = ta;
-    wb[warp] = tb;
-  }
   __syncthreads();
-  if (warp == 0) {
-    float va = wa[lane], vb = wb[lane];
+  if (warp < E) {
+    float va = ta[warp * 32 + lane], vb = tb[warp * 32 + lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const float na = __shfl_up_sync(0xffffffffu, va, o);
@@ -112,21 +124,26 @@ __device__ __forceinline__ void block_scan2(float (&a)[E], float (&b)[E], float*
         vb += nb;
       }
     }
-    wa[lane] = va;
-    wb[lane] = vb;
+    ta[warp * 32 + lane] = va;
+    tb[warp * 32 + lane] = vb;
   }
   __syncthreads();
-  const float oa = (ta - a[E - 1]) + (warp > 0 ? wa[warp - 1] : 0.f);
-  const float ob = (tb - b[E - 1]) + (warp > 0 ? wb[warp - 1] : 0.f);
+  float oa = 0.f, ob = 0.f;  // totals of the blocks before block e
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    a[e] += oa;
-    b[e] += ob;
+    const float pa = warp > 0 ? ta[e * 32 + warp - 1] : 0.f;
+    const float pb = warp > 0 ? tb[e * 32 + warp - 1] : 0.f;
+    a[e] += oa + pa;
+    b[e] += ob + pb;
+    oa += ta[e * 32 + 31];
+    ob += tb[e * 32 + 31];
   }
 }
 
 // out_r = sum_{m<nprev} P_m in_r (+ add) for input row r = blockIdx.x;
-// D <= E * 1024.  Rows, prefix arrays: 3 E 1024 floats of shared memory.
+// D <= E * 1024.  Thread t holds sorted positions and outputs t + e * 1024,
+// so every global access is coalesced; the row and the two prefix arrays sit
+// in 3 E 1024 floats of shared memory.
 template <int OP, int E>
 __global__ void __launch_bounds__(kApplyThreads)
     k_outer_apply(const float* __restrict__ in, int64_t ld_in, int D, int nprev, OuterSlot r0,
@@ -136,7 +153,8 @@ __global__ void __launch_bounds__(kApplyThreads)
   float* row = sm;
   float* A = row + E * kApplyThreads;
   float* B = A + E * kApplyThreads;
-  __shared__ float wa[32], wb[32], red[33];
+  __shared__ float tot[2 * E * 32];
+  __shared__ float red[33];
   const int t = threadIdx.x;
   const float* src = in + (int64_t)blockIdx.x * ld_in;
 #pragma unroll
@@ -166,46 +184,53 @@ __global__ void __launch_bounds__(kApplyThreads)
       continue;
     } else {
       const int* perm = r0.perm + m * stride;
-      const float* csort = r0.csort + m * stride;
+      const float* wsort = r0.wsort + m * stride;
       const int* ubi = r0.ubi + m * stride;
       constexpr int NP = (OP == MAPI_OP_MIN2) ? 2 : 1;
       float x0[E];
 #pragma unroll
       for (int pass = 0; pass < NP; ++pass) {
+        // every load of the pass is issued before the first use; positions
+        // past D read a zero of the row with a zero weight
         float a[E], b[E];
+        int pv[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const int p = t * E + e;
-          a[e] = b[e] = 0.f;
-          if (p < D) {
-            const int i = perm[p];
-            const float y = row[i];
-            const float z = pass == 0 ? sgnf(wt[i]) * y : y;
-            a[e] = csort[p] * z;
-            b[e] = z;
-          }
+          const int p = t + e * kApplyThreads;
+          pv[e] = p < D ? __ldg(perm + p) : p;
+          a[e] = p < D ? __ldg(wsort + p) : 0.f;
         }
-        block_scan2<E>(a, b, wa, wb);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          A[t * E + e] = a[e];
-          B[t * E + e] = b[e];
+          const float y = row[pv[e]];
+          const float z = pass == 0 ? sgnf(a[e]) * y : y;
+          a[e] = fabsf(a[e]) * z;
+          b[e] = z;
+        }
+        block_scan_strided<E>(a, b, tot);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          A[t + e * kApplyThreads] = a[e];
+          B[t + e * kApplyThreads] = b[e];
         }
         __syncthreads();
         const float totB = B[D - 1];
+        // outputs i = t + e * 1024 (past D: position 0, discarded)
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int i = t + e * kApplyThreads;
-          if (i < D) {
-            const float wi = wt[i];
-            const int q = ubi[i];
-            const float v = A[q] + fabsf(wi) * (totB - B[q]);
-            if (pass == 0) x0[e] = sgnf(wi) * v;
-            if constexpr (OP == MAPI_OP_MIN1) acc[e] += x0[e];
-            else if (pass == 1) acc[e] += 0.5f * (x0[e] + v);
-          }
+          pv[e] = i < D ? __ldg(ubi + i) : 0;
+          a[e] = i < D ? __ldg(wt + i) : 0.f;
         }
-        __syncthreads();  // A, B and the warp totals are reused
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int q = pv[e];
+          const float v = A[q] + fabsf(a[e]) * (totB - B[q]);
+          if (pass == 0) x0[e] = sgnf(a[e]) * v;
+          if constexpr (OP == MAPI_OP_MIN1) acc[e] += x0[e];
+          else if (pass == 1) acc[e] += 0.5f * (x0[e] + v);
+        }
+        __syncthreads();  // A, B and the block totals are reused
       }
     }
   }
@@ -218,21 +243,29 @@ __global__ void __launch_bounds__(kApplyThreads)
 }
 
 // Cc[i][j] = C[i][j] - T[j][i] for i, j < D (32 x 32 tiles through shared
-// memory); T's row j holds column j of sum_m P_m C (C is symmetric).
+// memory); T's row j holds column j of sum_m P_m C (C is symmetric).  The
+// tile of C is loaded with the tile of T, before the exchange.
 __global__ void __launch_bounds__(256)
     k_sub_transpose(const float* __restrict__ C, const float* __restrict__ T, int D, int64_t ld,
                     float* __restrict__ Cc) {
   __shared__ float tile[32][33];
   const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int rr = ty; rr < 32; rr += 8) {
+  float cv[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int rr = ty + 8 * u;
     const int j = bj + rr, i = bi + tx;
-    tile[rr][tx] = (j < D && i < D) ? T[(int64_t)j * ld + i] : 0.f;
+    tile[rr][tx] = (j < D && i < D) ? __ldcs(T + (int64_t)j * ld + i) : 0.f;
+    const int i2 = bi + rr, j2 = bj + tx;
+    cv[u] = (i2 < D && j2 < D) ? __ldcs(C + (int64_t)i2 * ld + j2) : 0.f;
   }
   __syncthreads();
-  for (int rr = ty; rr < 32; rr += 8) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int rr = ty + 8 * u;
     const int i = bi + rr, j = bj + tx;
-    if (i < D && j < D) Cc[(int64_t)i * ld + j] = C[(int64_t)i * ld + j] - tile[tx][rr];
+    if (i < D && j < D) Cc[(int64_t)i * ld + j] = cv[u] - tile[tx][rr];
   }
 }
 
@@ -286,7 +319,7 @@ OuterSlot outer_slot(void* base, int k, int64_t stride, int m) {
   float* f = (float*)base;
   s.wt = f + (int64_t)m * stride;
   s.perm = (int*)(f + (int64_t)k * stride) + (int64_t)m * stride;
-  s.csort = f + 2 * (int64_t)k * stride + (int64_t)m * stride;
+  s.wsort = f + 2 * (int64_t)k * stride + (int64_t)m * stride;
   s.ubi = (int*)(f + 3 * (int64_t)k * stride) + (int64_t)m * stride;
   return s;
 }
@@ -294,7 +327,7 @@ OuterSlot outer_slot(void* base, int k, int64_t stride, int m) {
 mapi_status outer_prepare(mapi_ctx* ctx) {
   MAPI_CUDA_TRY(ctx, cudaFuncSetAttribute((const void*)k_outer_prep,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(sizeof(float) * kOuterMaxD)));
+                                          (int)(sizeof(unsigned long long) * kOuterMaxD)));
   for (int E = 1; E <= 16; E *= 2) {
     const int smem = (int)(sizeof(float) * 3 * E * kApplyThreads);
     for (const void* fn : {apply_fn<MAPI_OP_MIN1>(E), apply_fn<MAPI_OP_MIN2>(E),
@@ -308,9 +341,11 @@ mapi_status outer_prepare(mapi_ctx* ctx) {
 mapi_status launch_outer_prep(mapi_ctx* ctx, mapi_op op, const float* w, int D, OuterSlot slot,
                               cudaStream_t s) {
   if (D < 1 || D > kOuterMaxD) return fail(ctx, MAPI_EINVAL, "outer product order outside 1..16384");
-  const size_t smem = sizeof(float) * (size_t)D;
-  k_outer_prep<<<(D + kPrepThreads - 1) / kPrepThreads, kPrepThreads, smem, s>>>(w, D, (int)op,
-                                                                                slot);
+  int Dp = 1;
+  while (Dp < D) Dp <<= 1;
+  if (Dp < 2) Dp = 2;
+  const size_t smem = sizeof(unsigned long long) * (size_t)Dp;
+  k_outer_prep<<<1, kPrepThreads, smem, s>>>(w, D, Dp, (int)op, slot);
   MAPI_CUDA_TRY(ctx, cudaGetLastError());
   count_launch(ctx);
   return MAPI_OK;

@@ -148,22 +148,40 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
-// Sum the splits of each tile in order, divide by denom, write C and its mirror.
-__global__ void k_mincov_reduce(const float* __restrict__ part, int ntiles, int nsplit, int D,
-                                float denom, float* __restrict__ C, int64_t ldc) {
+// Sum the splits of each tile in order, divide by denom, write C and its
+// mirror.  The tile goes through shared memory in 32 x 32 pieces so that the
+// mirror's rows are written whole.
+__global__ void __launch_bounds__(256)
+    k_mincov_reduce(const float* __restrict__ part, int ntiles, int nsplit, int D, float denom,
+                    float* __restrict__ C, int64_t ldc) {
+  __shared__ float piece[32][33];
   const int T = (D + kMcT - 1) / kMcT;
   int tp, tq;
   mc_tile_of(blockIdx.x, T, tp, tq);
-  for (int e = threadIdx.x; e < kMcT * kMcT; e += blockDim.x) {
-    const int i = e / kMcT, j = e % kMcT;
-    const int p = tp * kMcT + i, q = tq * kMcT + j;
-    if (p >= D || q >= D) continue;
-    float s = 0.f;
-    for (int k = 0; k < nsplit; ++k) s += part[((int64_t)k * ntiles + blockIdx.x) * kMcT * kMcT + e];
-    const float v = s / denom;
-    C[(int64_t)p * ldc + q] = v;
-    if (tp != tq) C[(int64_t)q * ldc + p] = v;
-  }
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int pi = 0; pi < kMcT; pi += 32)
+    for (int pj = 0; pj < kMcT; pj += 32) {
+      // rows pi.., columns pj.. of the tile: direct copy, kept for the mirror
+      for (int rr = ty; rr < 32; rr += 8) {
+        const int e = (pi + rr) * kMcT + pj + tx;
+        float sum = 0.f;
+        for (int k = 0; k < nsplit; ++k)
+          sum += part[((int64_t)k * ntiles + blockIdx.x) * kMcT * kMcT + e];
+        const float v = sum / denom;
+        piece[rr][tx] = v;
+        const int p = tp * kMcT + pi + rr, q = tq * kMcT + pj + tx;
+        if (p < D && q < D) C[(int64_t)p * ldc + q] = v;
+      }
+      __syncthreads();
+      if (tp != tq) {
+        // mirror: row q of C gets column q - tq*kMcT of the piece
+        for (int rr = ty; rr < 32; rr += 8) {
+          const int q = tq * kMcT + pj + rr, p = tp * kMcT + pi + tx;
+          if (p < D && q < D) C[(int64_t)q * ldc + p] = piece[tx][rr];
+        }
+      }
+      __syncthreads();
+    }
 }
 
 // ======================================================================
@@ -175,8 +193,9 @@ __global__ void k_mincov_reduce(const float* __restrict__ part, int ntiles, int 
 // +1); dot's is w (w . y).  wt is the component at unit l1 norm for min1 /
 // min2 (the unit of Eq. (8)'s iteration) and the kept unit-l2 component for
 // dot; launch_outer_prep ranks a finished component once: perm[p] = index
-// at sorted position p, csort[p] = its c, ubi[i] = last sorted position whose
-// c is <= c_i (ties included).
+// at sorted position p, wsort[p] = wt at that position (signed; its c is
+// |wsort[p]|), ubi[i] = last sorted position whose c is <= c_i (ties
+// included).
 // ======================================================================
 constexpr int kDeflMaxD = 1024;
 
@@ -186,9 +205,9 @@ struct DeflArgs {
   const float* P;     // outer-product vectors wt, column m at P + m * ldp
   int64_t ldp;
   const int* perm;    // [m][D_pad] per component (launch_outer_prep)
-  const float* csort;
+  const float* wsort;
   const int* ubi;
-  int64_t stride;     // elements between components in perm / csort / ubi
+  int64_t stride;     // elements between components in perm / wsort / ubi
 };
 
 // ======================================================================
@@ -323,7 +342,7 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
     for (int i = t; i < D; i += nt) {
       wm_s[i] = wm[i];
       if (!dot) {
-        cs_s[dpad(i)] = a.defl.csort[o + i];
+        cs_s[dpad(i)] = fabsf(a.defl.wsort[o + i]);
         perm_s[dpad(i)] = a.defl.perm[o + i];
         ub_s[i] = a.defl.ubi[o + i];
       }
@@ -1043,7 +1062,7 @@ mapi_status pca_enqueue(mapi_ctx* ctx, cudaStream_t s, const mapi_mat* X, const 
   defl.ldp = p.op == MAPI_OP_DOT ? D : p.D_pad;
   defl.stride = p.D_pad;
   defl.perm = slot0.perm;
-  defl.csort = slot0.csort;
+  defl.wsort = slot0.wsort;
   defl.ubi = slot0.ubi;
   for (int c = 0; c < k; ++c) {
     if (c > 0 && p.op != MAPI_OP_DOT) {
