@@ -332,19 +332,37 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
 
   // component m's vector, sorted |w| and the two index maps into group g's
   // padded arrays, loaded by the threads [t0, t0 + nt)
+  // (nt = 128 threads, D <= 1024: at most 8 entries per thread, all loaded
+  // before the first is stored)
   auto load_comp = [&](int m, int g, int t, int nt) {
+    constexpr int PER = kDeflMaxD / kEpiHalf;
     const float* wm = a.defl.P + (int64_t)m * a.defl.ldp;
     float* wm_s = arrays(g) + 4 * kDeflPadded;
     float* cs_s = wm_s + kDeflPadded;
     int* perm_s = reinterpret_cast<int*>(cs_s + kDeflPadded);
     int* ub_s = perm_s + kDeflPadded;
     const int64_t o = (int64_t)m * a.defl.stride;
-    for (int i = t; i < D; i += nt) {
-      wm_s[i] = wm[i];
-      if (!dot) {
-        cs_s[dpad(i)] = fabsf(a.defl.wsort[o + i]);
-        perm_s[dpad(i)] = a.defl.perm[o + i];
-        ub_s[i] = a.defl.ubi[o + i];
+    float vw[PER], vc[PER];
+    int vp[PER], vu[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = t + k * nt;
+      const bool in = i < D;
+      vw[k] = in ? __ldcg(wm + i) : 0.f;
+      vc[k] = (in && !dot) ? __ldcg(a.defl.wsort + o + i) : 0.f;
+      vp[k] = (in && !dot) ? __ldcg(a.defl.perm + o + i) : 0;
+      vu[k] = (in && !dot) ? __ldcg(a.defl.ubi + o + i) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = t + k * nt;
+      if (i < D) {
+        wm_s[i] = vw[k];
+        if (!dot) {
+          cs_s[dpad(i)] = fabsf(vc[k]);
+          perm_s[dpad(i)] = vp[k];
+          ub_s[i] = vu[k];
+        }
       }
     }
   };
@@ -533,21 +551,25 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
   float L = cluster_sum(cluster, &part[0], CS, &part[2]);
   if (a.norm_l2) L = sqrtf(L);
   const bool ok = (L > 0.f) && isfinite(L);
-  // 4. normalise own rows, delta
+  // 4. normalise own rows; the delta only when a stop rule needs it
+  const bool want_delta = a.ctl->tol > 0.f;
   Kahan dk;
   if (ok) {
     for (int i = threadIdx.x; i < RS; i += NT) {
       const int d = r0 + i;
       if (d >= D) continue;
       const float x = u[i] / L;  // the n divisions of §2.2
-      dk.add(fabsf(x - wo[i]));
+      if (want_delta) dk.add(fabsf(x - wo[i]));
       a.w_next[d] = x;
     }
   }
-  const float dp = block_sum<NT>(dk.value(), red);
-  if (threadIdx.x == 0) part[1] = dp;
-  cluster.sync();
-  const float Dsum = (r == 0) ? cluster_sum(cluster, &part[1], CS, &part[3]) : 0.f;
+  float Dsum = 0.f;
+  if (want_delta) {
+    const float dp = block_sum<NT>(dk.value(), red);
+    if (threadIdx.x == 0) part[1] = dp;
+    cluster.sync();
+    if (r == 0) Dsum = cluster_sum(cluster, &part[1], CS, &part[3]);
+  }
   if (r == 0 && threadIdx.x == 0) {
     VecState* st = &a.ctl->v[0];
     if (!ok) {
@@ -555,9 +577,9 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
       st->done = 1;
     } else {
       st->iters += 1;
-      st->delta = Dsum;
+      if (want_delta) st->delta = Dsum;
       st->norm = L;
-      if (a.ctl->tol > 0.f && Dsum < a.ctl->tol) st->done = 1;
+      if (want_delta && Dsum < a.ctl->tol) st->done = 1;
     }
     a.ctl->all_done = st->done;
     a.ctl->counter = 0;
