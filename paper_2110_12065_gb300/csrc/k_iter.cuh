@@ -10,9 +10,21 @@
 //   k_finish_*  Alg. 1 step 6 (optional): w_T / ||w_T||_2, written out.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "device_common.cuh"
 
 namespace mapi {
+
+namespace cgk = cooperative_groups;
+
+// K1 on large BF16 and integer matrices runs in clusters of this many CTAs
+// along the rows, and the cluster that finishes last runs the epilogue with
+// all its threads (measured at n = 16384, BF16: 112 -> 103 us per step; FP32
+// unchanged, FP8 and small matrices slower, so they keep the one-CTA
+// epilogue).
+constexpr int kGemvCluster = 8;
+constexpr int kGemvClusterMinRows = 4096;
 
 struct GemvArgs {
   const uint8_t* A;     // rows_pad x ld elements, 16-byte rows
@@ -119,18 +131,125 @@ __device__ void epilogue_float(const GemvArgs& g, int ks) {
   }
 }
 
-// K1: y = A (+) w for V vectors, R rows per warp, WARPS warps per CTA.
-template <int OP, int ST, int V, int R, int WARPS>
+// The same epilogue run by all CS CTAs of the last cluster: thread t of CTA
+// r takes rows r NT + t, r NT + t + CS NT, ... (kEpiU of them in flight) in
+// both passes, so it reads back only what it wrote; the norm and delta are
+// block sums added over the cluster in rank order.
+template <int NT, int V, int CS>
+__device__ void epilogue_float_cluster(const GemvArgs& g, int ks, cgk::cluster_group& cluster) {
+  constexpr int kEpiU = 8;
+  constexpr int NTC = NT * CS;
+  __shared__ float sh[33];
+  __shared__ float part[2];
+  const int cr = (int)cluster.block_rank();
+  const int tg = cr * NT + threadIdx.x;
+  for (int v = 0; v < V; ++v) {
+    VecState* st = &g.ctl->v[v];
+    if (*(volatile int*)&st->done) continue;  // uniform: written by earlier launches
+    float* y0 = g.ypart + (int64_t)v * g.rows_pad;
+    Kahan acc;
+    for (int i0 = tg; i0 < g.n; i0 += NTC * kEpiU) {
+      float yv[kEpiU];
+#pragma unroll
+      for (int u = 0; u < kEpiU; ++u) {
+        const int i = i0 + u * NTC;
+        yv[u] = i < g.n ? __ldcg(y0 + i) : 0.f;
+      }
+      for (int k = 1; k < ks; ++k) {
+        const float* yk = g.ypart + ((int64_t)k * V + v) * g.rows_pad;
+        float pk[kEpiU];
+#pragma unroll
+        for (int u = 0; u < kEpiU; ++u) {
+          const int i = i0 + u * NTC;
+          pk[u] = i < g.n ? __ldcg(yk + i) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kEpiU; ++u) yv[u] += pk[u];
+      }
+#pragma unroll
+      for (int u = 0; u < kEpiU; ++u) {
+        const int i = i0 + u * NTC;
+        if (i < g.n) {
+          if (ks > 1) y0[i] = yv[u];
+          acc.add(g.norm_l2 ? yv[u] * yv[u] : fabsf(yv[u]));
+        }
+      }
+    }
+    const float lp = block_sum<NT>(acc.value(), sh);
+    if (threadIdx.x == 0) part[0] = lp;
+    cluster.sync();
+    float L = 0.f;
+#pragma unroll
+    for (int q = 0; q < CS; ++q) L += *cluster.map_shared_rank(&part[0], q);
+    if (g.norm_l2) L = sqrtf(L);
+    if (!(L > 0.f) || !isfinite(L)) {
+      if (cr == 0 && threadIdx.x == 0) {
+        st->status = (L == 0.f) ? MAPI_EZERONORM : MAPI_ENONFINITE;
+        st->done = 1;
+      }
+      cluster.sync();  // part[0] is read by every rank before it changes
+      continue;
+    }
+    const float* wo = g.w + (int64_t)v * g.wst;
+    float* wn = g.w_next + (int64_t)v * g.wst;
+    Kahan dl;
+    for (int i0 = tg; i0 < g.n; i0 += NTC * kEpiU) {
+      float yv[kEpiU], wv[kEpiU];
+#pragma unroll
+      for (int u = 0; u < kEpiU; ++u) {
+        const int i = i0 + u * NTC;
+        yv[u] = i < g.n ? ((ks > 1) ? y0[i] : __ldcg(y0 + i)) : 0.f;
+        wv[u] = i < g.n ? wo[i] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kEpiU; ++u) {
+        const int i = i0 + u * NTC;
+        if (i < g.n) {
+          const float x = yv[u] / L;  // the n divisions of §2.2
+          dl.add(fabsf(x - wv[u]));
+          wn[i] = x;
+        }
+      }
+    }
+    const float dp = block_sum<NT>(dl.value(), sh);
+    if (threadIdx.x == 0) part[1] = dp;
+    cluster.sync();
+    if (cr == 0 && threadIdx.x == 0) {
+      float D = 0.f;
+#pragma unroll
+      for (int q = 0; q < CS; ++q) D += *cluster.map_shared_rank(&part[1], q);
+      st->iters += 1;
+      st->delta = D;
+      st->norm = L;
+      if (g.ctl->tol > 0.f && D < g.ctl->tol) st->done = 1;
+    }
+    cluster.sync();  // part[] is read by rank 0 (and every rank) before it changes
+  }
+  if (cr == 0 && threadIdx.x == 0) {
+    int all = 1;
+    for (int v = 0; v < V; ++v) all &= ((volatile int*)&g.ctl->v[v].done)[0];
+    g.ctl->all_done = all;
+    g.ctl->counter = 0;
+    __threadfence();
+  }
+}
+
+// K1: y = A (+) w for V vectors, R rows per warp, WARPS warps per CTA; CL
+// CTAs per cluster (1: the last CTA alone runs the epilogue).
+template <int OP, int ST, int V, int R, int WARPS, int CL>
 __global__ void __launch_bounds__(WARPS * 32)
     k1_gemv_float(GemvArgs g) {
   if (*(volatile int*)&g.ctl->all_done) return;
   using Ch = Chunk<ST>;
   constexpr int E = Ch::E;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row0 = (blockIdx.x * WARPS + warp) * R;
+  // CTAs past the padded rows (the grid is a whole number of clusters) only
+  // take part in the election
+  const bool rows_here = blockIdx.x * WARPS * R < g.rows_pad;
+  const int row0 = rows_here ? (blockIdx.x * WARPS + warp) * R : 0;
   const int ks = blockIdx.y;
   const int c_beg = ks * g.seg;
-  const int c_end = min(g.chunks, c_beg + g.seg);
+  const int c_end = rows_here ? min(g.chunks, c_beg + g.seg) : c_beg;
 
   float acc[R][V][2];
 #pragma unroll
@@ -209,11 +328,32 @@ __global__ void __launch_bounds__(WARPS * 32)
       float s = acc[r][v][0] + acc[r][v][1];
 #pragma unroll
       for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) g.ypart[((int64_t)ks * V + v) * g.rows_pad + row0 + r] = s;
+      if (lane == 0 && rows_here) g.ypart[((int64_t)ks * V + v) * g.rows_pad + row0 + r] = s;
     }
 
-  if (!elect_last_cta(&g.ctl->counter, gridDim.x * gridDim.y)) return;
-  epilogue_float<WARPS * 32, V>(g, gridDim.y);
+  if constexpr (CL == 1) {
+    if (!elect_last_cta(&g.ctl->counter, gridDim.x * gridDim.y)) return;
+    epilogue_float<WARPS * 32, V>(g, gridDim.y);
+  } else {
+    // last-cluster election: every CTA takes a ticket once its partials are
+    // visible; the cluster holding the last ticket runs the epilogue
+    cgk::cluster_group cluster = cgk::this_cluster();
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned t = atomicAdd(&g.ctl->counter, 1u);
+      s_last = (t == gridDim.x * gridDim.y - 1) ? 1 : 0;
+    }
+    cluster.sync();
+    int last = 0;
+#pragma unroll
+    for (int q = 0; q < CL; ++q) last |= *cluster.map_shared_rank(&s_last, q);
+    cluster.sync();  // every rank has read the tickets
+    if (!last) return;
+    __threadfence();
+    epilogue_float_cluster<WARPS * 32, V, CL>(g, gridDim.y, cluster);
+  }
 }
 
 // ------------------------------------------------------------ integer path
@@ -223,22 +363,45 @@ struct IGemvArgs {
   int q;
 };
 
-template <int NT, int V>
+// Integer epilogue, run by the CS CTAs of the last cluster (CS = 1: the last
+// CTA); thread t of CTA r takes rows r NT + t, r NT + t + CS NT, ...  Every
+// sum is an exact INT64 sum, so the split changes no result.
+template <int NT, int V, int CS>
 __device__ void epilogue_int(const IGemvArgs& a, int ks) {
   constexpr int kEpiU = 8;  // rows per thread in flight (see epilogue_float)
+  constexpr int NTC = NT * CS;
   const GemvArgs& g = a.g;
   __shared__ long long sh[33];
+  __shared__ long long part[2];
+  int cr = 0;
+  if constexpr (CS > 1) cr = (int)cgk::this_cluster().block_rank();
+  const int tg = cr * NT + threadIdx.x;
+  // the CTA totals of slot k added over the cluster (after a cluster barrier)
+  auto total = [&](int k, long long mine) {
+    if constexpr (CS == 1) {
+      return mine;
+    } else {
+      if (threadIdx.x == 0) part[k] = mine;
+      cgk::cluster_group cl = cgk::this_cluster();
+      cl.sync();
+      long long t = 0;
+#pragma unroll
+      for (int q = 0; q < CS; ++q) t += *cl.map_shared_rank(&part[k], q);
+      cl.sync();  // every rank has read part[k]
+      return t;
+    }
+  };
   const int* ypart = reinterpret_cast<const int*>(g.ypart);
   for (int v = 0; v < V; ++v) {
     VecState* st = &g.ctl->v[v];
     if (*(volatile int*)&st->done) continue;
     int* y0 = reinterpret_cast<int*>(g.ypart) + (int64_t)v * g.rows_pad;
     long long s = 0;
-    for (int i0 = threadIdx.x; i0 < g.n; i0 += NT * kEpiU) {
+    for (int i0 = tg; i0 < g.n; i0 += NTC * kEpiU) {
       int yv[kEpiU];
 #pragma unroll
       for (int u = 0; u < kEpiU; ++u) {
-        const int i = i0 + u * NT;
+        const int i = i0 + u * NTC;
         yv[u] = i < g.n ? __ldcg(y0 + i) : 0;
       }
       for (int k = 1; k < ks; ++k) {
@@ -246,7 +409,7 @@ __device__ void epilogue_int(const IGemvArgs& a, int ks) {
         int pk[kEpiU];
 #pragma unroll
         for (int u = 0; u < kEpiU; ++u) {
-          const int i = i0 + u * NT;
+          const int i = i0 + u * NTC;
           pk[u] = i < g.n ? __ldcg(yk + i) : 0;
         }
 #pragma unroll
@@ -254,16 +417,16 @@ __device__ void epilogue_int(const IGemvArgs& a, int ks) {
       }
 #pragma unroll
       for (int u = 0; u < kEpiU; ++u) {
-        const int i = i0 + u * NT;
+        const int i = i0 + u * NTC;
         if (i < g.n) {
           if (ks > 1) y0[i] = yv[u];
           s += (long long)abs(yv[u]);
         }
       }
     }
-    const long long L = block_sum_i64<NT>(s, sh);
+    const long long L = total(0, block_sum_i64<NT>(s, sh));
     if (L == 0) {
-      if (threadIdx.x == 0) {
+      if (cr == 0 && threadIdx.x == 0) {
         st->status = MAPI_EZERONORM;
         st->done = 1;
       }
@@ -273,27 +436,41 @@ __device__ void epilogue_int(const IGemvArgs& a, int ks) {
     int* wn = reinterpret_cast<int*>(g.w_next) + (int64_t)v * g.wst;
     long long d = 0;
     const long long half = L / 2;
-    for (int i0 = threadIdx.x; i0 < g.n; i0 += NT * kEpiU) {
+    // floor(N / L) for the n divisions: an FP32 estimate from one reciprocal
+    // of L, made exact by whole steps of L on the remainder (the quotient is
+    // at most 2^24 + 1, so the estimate is within a few units)
+    const float rL = 1.f / (float)L;
+    for (int i0 = tg; i0 < g.n; i0 += NTC * kEpiU) {
       int yv[kEpiU], wv[kEpiU];
 #pragma unroll
       for (int u = 0; u < kEpiU; ++u) {
-        const int i = i0 + u * NT;
+        const int i = i0 + u * NTC;
         yv[u] = i < g.n ? ((ks > 1) ? y0[i] : __ldcg(y0 + i)) : 0;
         wv[u] = i < g.n ? wo[i] : 0;
       }
 #pragma unroll
       for (int u = 0; u < kEpiU; ++u) {
-        const int i = i0 + u * NT;
+        const int i = i0 + u * NTC;
         if (i < g.n) {
-          const long long m = (((long long)abs(yv[u]) << a.q) + half) / L;
+          const long long N = ((long long)abs(yv[u]) << a.q) + half;
+          long long m = (long long)((float)N * rL);
+          long long rem = N - m * L;
+          while (rem < 0) {
+            --m;
+            rem += L;
+          }
+          while (rem >= L) {
+            ++m;
+            rem -= L;
+          }
           const int x = yv[u] < 0 ? -(int)m : (int)m;
           d += (long long)abs(x - wv[u]);
           wn[i] = x;
         }
       }
     }
-    const long long D = block_sum_i64<NT>(d, sh);
-    if (threadIdx.x == 0) {
+    const long long D = total(1, block_sum_i64<NT>(d, sh));
+    if (cr == 0 && threadIdx.x == 0) {
       st->iters += 1;
       st->idelta = D;
       st->delta = (float)D;
@@ -301,7 +478,7 @@ __device__ void epilogue_int(const IGemvArgs& a, int ks) {
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (cr == 0 && threadIdx.x == 0) {
     int all = 1;
     for (int v = 0; v < V; ++v) all &= ((volatile int*)&g.ctl->v[v].done)[0];
     g.ctl->all_done = all;
@@ -310,7 +487,7 @@ __device__ void epilogue_int(const IGemvArgs& a, int ks) {
   }
 }
 
-template <int OP, int ST, int V, int R, int WARPS>
+template <int OP, int ST, int V, int R, int WARPS, int CL>
 __global__ void __launch_bounds__(WARPS * 32)
     k1_gemv_int(IGemvArgs a) {
   const GemvArgs& g = a.g;
@@ -318,10 +495,12 @@ __global__ void __launch_bounds__(WARPS * 32)
   using Ch = Chunk<ST>;
   constexpr int E = Ch::E;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row0 = (blockIdx.x * WARPS + warp) * R;
+  // CTAs past the padded rows (a whole number of clusters) only vote
+  const bool rows_here = blockIdx.x * WARPS * R < g.rows_pad;
+  const int row0 = rows_here ? (blockIdx.x * WARPS + warp) * R : 0;
   const int ks = blockIdx.y;
   const int c_beg = ks * g.seg;
-  const int c_end = min(g.chunks, c_beg + g.seg);
+  const int c_end = rows_here ? min(g.chunks, c_beg + g.seg) : c_beg;
   int acc[R][V];
 #pragma unroll
   for (int r = 0; r < R; ++r)
@@ -361,11 +540,30 @@ __global__ void __launch_bounds__(WARPS * 32)
       int s = acc[r][v];
 #pragma unroll
       for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0)
+      if (lane == 0 && rows_here)
         reinterpret_cast<int*>(g.ypart)[((int64_t)ks * V + v) * g.rows_pad + row0 + r] = s;
     }
-  if (!elect_last_cta(&g.ctl->counter, gridDim.x * gridDim.y)) return;
-  epilogue_int<WARPS * 32, V>(a, gridDim.y);
+  if constexpr (CL == 1) {
+    if (!elect_last_cta(&g.ctl->counter, gridDim.x * gridDim.y)) return;
+  } else {
+    // last-cluster election (as in k1_gemv_float)
+    cgk::cluster_group cluster = cgk::this_cluster();
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned t = atomicAdd(&g.ctl->counter, 1u);
+      s_last = (t == gridDim.x * gridDim.y - 1) ? 1 : 0;
+    }
+    cluster.sync();
+    int last = 0;
+#pragma unroll
+    for (int q = 0; q < CL; ++q) last |= *cluster.map_shared_rank(&s_last, q);
+    cluster.sync();  // every rank has read the tickets
+    if (!last) return;
+    __threadfence();
+  }
+  epilogue_int<WARPS * 32, V, CL>(a, gridDim.y);
 }
 
 // Launch table entry points (defined per storage file).
@@ -387,8 +585,24 @@ constexpr int kWarps = 8;  // warps per CTA
   template <int OP, int V>                                                        \
   static cudaError_t launch_##FNNAME(dim3 grid, cudaStream_t s, const GemvArgs& g, \
                                      int) {                                       \
-    k1_gemv_float<OP, ST, V, kR, kWarps><<<grid, kWarps * 32, 0, s>>>(g);         \
-    return cudaGetLastError();                                                    \
+    if (ST != kBF16 || g.n < kGemvClusterMinRows) {                               \
+      k1_gemv_float<OP, ST, V, kR, kWarps, 1><<<grid, kWarps * 32, 0, s>>>(g);    \
+      return cudaGetLastError();                                                  \
+    }                                                                             \
+    cudaLaunchConfig_t cfg = {};                                                  \
+    cudaLaunchAttribute attr[1];                                                  \
+    attr[0].id = cudaLaunchAttributeClusterDimension;                             \
+    attr[0].val.clusterDim.x = kGemvCluster;                                      \
+    attr[0].val.clusterDim.y = 1;                                                 \
+    attr[0].val.clusterDim.z = 1;                                                 \
+    cfg.gridDim = dim3((grid.x + kGemvCluster - 1) / kGemvCluster * kGemvCluster, \
+                       grid.y, 1);                                                \
+    cfg.blockDim = dim3(kWarps * 32, 1, 1);                                       \
+    cfg.stream = s;                                                               \
+    cfg.attrs = attr;                                                             \
+    cfg.numAttrs = 1;                                                             \
+    return cudaLaunchKernelEx(&cfg, k1_gemv_float<OP, ST, V, kR, kWarps,          \
+                                                  (ST == kBF16 ? kGemvCluster : 1)>, g); \
   }                                                                               \
   LaunchFn FNNAME(int op, int V) {                                                \
     switch (op * 16 + V) {                                                        \

@@ -6,8 +6,22 @@ namespace mapi {
 template <int OP, int ST, int V>
 static cudaError_t launch_int(dim3 grid, cudaStream_t s, const GemvArgs& g, int q) {
   IGemvArgs a{g, q};
-  k1_gemv_int<OP, ST, V, kR, kWarps><<<grid, kWarps * 32, 0, s>>>(a);
-  return cudaGetLastError();
+  if (g.n < kGemvClusterMinRows) {
+    k1_gemv_int<OP, ST, V, kR, kWarps, 1><<<grid, kWarps * 32, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kGemvCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((grid.x + kGemvCluster - 1) / kGemvCluster * kGemvCluster, grid.y, 1);
+  cfg.blockDim = dim3(kWarps * 32, 1, 1);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k1_gemv_int<OP, ST, V, kR, kWarps, kGemvCluster>, a);
 }
 
 template <int ST>

@@ -275,6 +275,38 @@ def test_integer_storage_bit_exact(mapi_ctx, st, bits, op, n):
         M.mapi_matrix_free(mapi_ctx, mat)
 
 
+@pytest.mark.parametrize("st", ["i16", "i8", "bf16"])
+@pytest.mark.parametrize("op", ["min1", "min2"])
+def test_large_matrices_take_the_cluster_epilogue(mapi_ctx, st, op):
+    """n = 5000 (>= 4096): BF16 and integer storage run K1 in clusters whose
+    last one normalises; the grid is padded to whole clusters (316 row
+    blocks -> 320).  Integer storage stays bit-exact, BF16 within 1e-5 of
+    the oracle on the stored values."""
+    n = 5000
+    r = datagen.rng(77)
+    # entries near 2^-10: int8 then takes the scale 2^17, fine enough for a
+    # unit-l1 vector of 5000 entries (at 2^7 it would round to zero)
+    A = (r.uniform(-0.9, 0.9, size=(n, n)) * 2.0 ** -10).astype(np.float32)
+    if op == "min2":
+        A = np.abs(A)
+    w0 = r.uniform(0.0, 1.0, size=n).astype(np.float32)
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(A), st)
+    try:
+        w, it, dl = gpu_iter(mapi_ctx, mat, op, w0, 3)
+        assert it[0] == 3
+        if st == "bf16":
+            _, want, _, _ = oracle.mapi(op, oracle.quant_bf16(A), w0.astype(np.float64), 3)
+            assert rel_l1(w, want) <= TOL32
+        else:
+            q = oracle.int_scale(A, 16 if st == "i16" else 8)
+            ost, want, oit, odl = oracle.mapi_int(op, oracle.quant_int(A, q), q, w0, 3)
+            assert ost == oracle.OK and oit == 3
+            np.testing.assert_array_equal(np.rint(w * 2.0 ** q).astype(np.int64), want)
+            assert dl[0] * 2.0 ** q == odl
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
+
+
 def test_full_size_one_step_f32(mapi_ctx):
     """n = 16384 (the dense PageRank size), one step from a fixed iterate,
     against the oracle's full product."""
