@@ -574,8 +574,19 @@ LaunchFn gemv_lookup_bf16(int op, int V);
 LaunchFn gemv_lookup_fp8(int op, int V);
 LaunchFn gemv_lookup_int(int st, int op, int V);
 
-constexpr int kR = 2;      // rows per warp
+constexpr int kR = 2;      // rows per warp (FP32)
 constexpr int kWarps = 8;  // warps per CTA
+
+// Rows per warp by storage: every load of w serves R rows.  FP8 and the
+// integer formats take 4 (w's L1 traffic was twice A's for FP8 at 2 rows;
+// measured at n = 16384: FP8 98 -> 88 us, I16 120 -> 109 us per step); BF16
+// stays at 2 (4 measured slower: 103 -> 115 us).
+constexpr int kRowsNarrow = 4;
+template <int ST>
+constexpr int gemv_rows() { return (ST == kF32 || ST == kBF16) ? kR : kRowsNarrow; }
+inline int gemv_rows_for(mapi_storage st) {
+  return (st == MAPI_ST_F32 || st == MAPI_ST_BF16) ? kR : kRowsNarrow;
+}
 
 }  // namespace mapi
 
@@ -586,7 +597,8 @@ constexpr int kWarps = 8;  // warps per CTA
   static cudaError_t launch_##FNNAME(dim3 grid, cudaStream_t s, const GemvArgs& g, \
                                      int) {                                       \
     if (ST != kBF16 || g.n < kGemvClusterMinRows) {                               \
-      k1_gemv_float<OP, ST, V, kR, kWarps, 1><<<grid, kWarps * 32, 0, s>>>(g);    \
+      k1_gemv_float<OP, ST, V, gemv_rows<ST>(), kWarps, 1>                        \
+          <<<grid, kWarps * 32, 0, s>>>(g);                                       \
       return cudaGetLastError();                                                  \
     }                                                                             \
     cudaLaunchConfig_t cfg = {};                                                  \
@@ -601,7 +613,7 @@ constexpr int kWarps = 8;  // warps per CTA
     cfg.stream = s;                                                               \
     cfg.attrs = attr;                                                             \
     cfg.numAttrs = 1;                                                             \
-    return cudaLaunchKernelEx(&cfg, k1_gemv_float<OP, ST, V, kR, kWarps,          \
+    return cudaLaunchKernelEx(&cfg, k1_gemv_float<OP, ST, V, gemv_rows<ST>(), kWarps, \
                                                   (ST == kBF16 ? kGemvCluster : 1)>, g); \
   }                                                                               \
   LaunchFn FNNAME(int op, int V) {                                                \

@@ -7,7 +7,7 @@ template <int OP, int ST, int V>
 static cudaError_t launch_int(dim3 grid, cudaStream_t s, const GemvArgs& g, int q) {
   IGemvArgs a{g, q};
   if (g.n < kGemvClusterMinRows) {
-    k1_gemv_int<OP, ST, V, kR, kWarps, 1><<<grid, kWarps * 32, 0, s>>>(a);
+    k1_gemv_int<OP, ST, V, gemv_rows<ST>(), kWarps, 1><<<grid, kWarps * 32, 0, s>>>(a);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -21,7 +21,7 @@ static cudaError_t launch_int(dim3 grid, cudaStream_t s, const GemvArgs& g, int 
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k1_gemv_int<OP, ST, V, kR, kWarps, kGemvCluster>, a);
+  return cudaLaunchKernelEx(&cfg, k1_gemv_int<OP, ST, V, gemv_rows<ST>(), kWarps, kGemvCluster>, a);
 }
 
 template <int ST>

@@ -164,9 +164,9 @@ mapi_status launch_finish(mapi_ctx* ctx, cudaStream_t s, const float* wb0, const
 GemvPlan plan_gemv(const mapi_ctx* ctx, const mapi_mat* A, int nvec) {
   (void)nvec;
   GemvPlan p;
-  p.rows_per_warp = kR;
+  p.rows_per_warp = gemv_rows_for(A->storage);
   p.warps = kWarps;
-  p.grid_rows = A->rows_pad / (kR * kWarps);
+  p.grid_rows = A->rows_pad / (p.rows_per_warp * kWarps);
   const int64_t chunks = A->ld * elem_bytes(A->storage) / 16;
   // enough CTAs for several waves (the block scheduler then balances the
   // tail), each column split still >= 64 chunks (2 per lane)
