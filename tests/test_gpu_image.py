@@ -47,6 +47,22 @@ def test_project_matches_oracle(mapi_ctx, op, D, k, rows):
         assert rel_l1(out[i] - m, want[i] - m) <= TOL, i
 
 
+@pytest.mark.parametrize("op", ["min1", "min2", "dot"])
+@pytest.mark.parametrize("D,k", [(2048, 1), (2049, 2), (8193, 1), (128, 64)])
+def test_project_width_boundaries_and_most_components(mapi_ctx, op, D, k):
+    W = components(D, k, seed=3 * D + k)
+    Z = datagen.rng(D + 1).standard_normal((2, D)).astype(np.float32)
+    out = to_host(M.mapi_mavp_project(mapi_ctx, op, to_dev(W), to_dev(Z)))
+    want = oracle.reconstruct(op, W.T, Z.T.astype(np.float64), np.zeros(D)).T
+    assert rel_l1(out, want) <= TOL
+
+
+def test_project_no_rows(mapi_ctx):
+    W = to_dev(components(64, 2, seed=1))
+    out = M.mapi_mavp_project(mapi_ctx, "min1", W, torch.empty((0, 64), device="cuda"))
+    assert out.shape == (0, 64)
+
+
 def test_project_without_offset_and_ties(mapi_ctx):
     """Components with many equal magnitudes (ties in the ranking) and zeros."""
     D = 2048
