@@ -40,6 +40,7 @@ struct GemvArgs {
   IterCtl* ctl;
   const float* row_mult;  // FP8: 2^(120 + k_i) per row; else unused
   int norm_l2;          // 1 for DOT (Eq. (1)), 0 for the MAVPs (Eq. (6))
+  int clusters;         // 1: large BF16 / integer matrices may run in clusters
 };
 
 constexpr int kEpiThreads = 256;
@@ -596,7 +597,7 @@ inline int gemv_rows_for(mapi_storage st) {
   template <int OP, int V>                                                        \
   static cudaError_t launch_##FNNAME(dim3 grid, cudaStream_t s, const GemvArgs& g, \
                                      int) {                                       \
-    if (ST != kBF16 || g.n < kGemvClusterMinRows) {                               \
+    if (ST != kBF16 || g.n < kGemvClusterMinRows || !g.clusters) {                \
       k1_gemv_float<OP, ST, V, gemv_rows<ST>(), kWarps, 1>                        \
           <<<grid, kWarps * 32, 0, s>>>(g);                                       \
       return cudaGetLastError();                                                  \

@@ -6,7 +6,7 @@ namespace mapi {
 template <int OP, int ST, int V>
 static cudaError_t launch_int(dim3 grid, cudaStream_t s, const GemvArgs& g, int q) {
   IGemvArgs a{g, q};
-  if (g.n < kGemvClusterMinRows) {
+  if (g.n < kGemvClusterMinRows || !g.clusters) {
     k1_gemv_int<OP, ST, V, gemv_rows<ST>(), kWarps, 1><<<grid, kWarps * 32, 0, s>>>(a);
     return cudaGetLastError();
   }

@@ -181,7 +181,7 @@ extern "C" mapi_status mapi_iterate_noalloc(const float* A, int n, int64_t lda, 
   cudaStream_t s = (cudaStream_t)cuda_stream;
 
   const int64_t wst = ((int64_t)n + 15) / 16 * 16;
-  GemvArgs g;
+  GemvArgs g{};
   g.A = (const uint8_t*)A;
   g.row_bytes = lda * 4;
   g.chunks = (n + 3) / 4;

@@ -591,6 +591,7 @@ mapi_status ensure_server(mapi_ctx* ctx, Server** out) {
       delete sv;
       return s;
     }
+    sv->child->gemv_clusters = false;
     {
       int prev = 0;
       cudaGetDevice(&prev);

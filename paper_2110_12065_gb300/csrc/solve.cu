@@ -242,6 +242,7 @@ mapi_status enqueue_solve(mapi_ctx* ctx, cudaStream_t stream, const mapi_mat* A,
   g.ctl = ctl;
   g.row_mult = A->row_scale;
   g.norm_l2 = (op == MAPI_OP_DOT) ? 1 : 0;
+  g.clusters = ctx->gemv_clusters ? 1 : 0;
   const dim3 grid(p.grid_rows, p.ksplit);
   // algorithmic work of one step: the stored matrix once (plus FP8 row
   // scales), n^2 terms per vector
