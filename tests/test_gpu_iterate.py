@@ -275,13 +275,13 @@ def test_integer_storage_bit_exact(mapi_ctx, st, bits, op, n):
         M.mapi_matrix_free(mapi_ctx, mat)
 
 
-@pytest.mark.parametrize("st", ["i16", "i8", "bf16"])
+@pytest.mark.parametrize("st", ["i16", "i8", "bf16", "fp8"])
 @pytest.mark.parametrize("op", ["min1", "min2"])
 def test_large_matrices_take_the_cluster_epilogue(mapi_ctx, st, op):
-    """n = 5000 (>= 4096): BF16 and integer storage run K1 in clusters whose
-    last one normalises; the grid is padded to whole clusters (316 row
-    blocks -> 320).  Integer storage stays bit-exact, BF16 within 1e-5 of
-    the oracle on the stored values."""
+    """n = 5000 (>= 4096): BF16, FP8 and integer storage run K1 in clusters whose
+    last one normalises; the grid is padded to whole clusters.  Integer
+    storage stays bit-exact, BF16 and FP8 within 1e-5 of the oracle on the
+    stored values."""
     n = 5000
     r = datagen.rng(77)
     # entries near 2^-10: int8 then takes the scale 2^17, fine enough for a
@@ -294,8 +294,9 @@ def test_large_matrices_take_the_cluster_epilogue(mapi_ctx, st, op):
     try:
         w, it, dl = gpu_iter(mapi_ctx, mat, op, w0, 3)
         assert it[0] == 3
-        if st == "bf16":
-            _, want, _, _ = oracle.mapi(op, oracle.quant_bf16(A), w0.astype(np.float64), 3)
+        if st in ("bf16", "fp8"):
+            deq = oracle.quant_bf16(A) if st == "bf16" else oracle.quant_fp8_rows(A)[0]
+            _, want, _, _ = oracle.mapi(op, deq, w0.astype(np.float64), 3)
             assert rel_l1(w, want) <= TOL32
         else:
             q = oracle.int_scale(A, 16 if st == "i16" else 8)
