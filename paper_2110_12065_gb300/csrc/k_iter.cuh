@@ -18,11 +18,11 @@ namespace mapi {
 
 namespace cgk = cooperative_groups;
 
-// K1 on large BF16, FP8 and integer matrices runs in clusters of this many
-// CTAs along the rows, and the cluster that finishes last runs the epilogue
-// with all its threads (measured at n = 16384: BF16 112 -> 103, FP8 88 -> 79
-// us per step; FP32 unchanged and small matrices slower, so they keep the
-// one-CTA epilogue).
+// K1 on matrices of n >= 4096 runs in clusters of this many CTAs along the
+// rows, and the cluster that finishes last runs the epilogue with all its
+// threads (measured: BF16 112 -> 103 and FP8 88 -> 79 us per step at n =
+// 16384; FP32 43 -> 37 at n = 4096, 69 -> 55 at 6144, unchanged at 16384;
+// small matrices are slower in clusters and keep the one-CTA epilogue).
 constexpr int kGemvCluster = 8;
 constexpr int kGemvClusterMinRows = 4096;
 
@@ -40,7 +40,7 @@ struct GemvArgs {
   IterCtl* ctl;
   const float* row_mult;  // FP8: 2^(120 + k_i) per row; else unused
   int norm_l2;          // 1 for DOT (Eq. (1)), 0 for the MAVPs (Eq. (6))
-  int clusters;         // 1: large BF16 / integer matrices may run in clusters
+  int clusters;         // 1: matrices of n >= kGemvClusterMinRows may run in clusters
 };
 
 constexpr int kEpiThreads = 256;
@@ -597,7 +597,7 @@ inline int gemv_rows_for(mapi_storage st) {
   template <int OP, int V>                                                        \
   static cudaError_t launch_##FNNAME(dim3 grid, cudaStream_t s, const GemvArgs& g, \
                                      int) {                                       \
-    if ((ST != kBF16 && ST != kFP8) || g.n < kGemvClusterMinRows || !g.clusters) { \
+    if (g.n < kGemvClusterMinRows || !g.clusters) {                               \
       k1_gemv_float<OP, ST, V, gemv_rows<ST>(), kWarps, 1>                        \
           <<<grid, kWarps * 32, 0, s>>>(g);                                       \
       return cudaGetLastError();                                                  \
@@ -615,7 +615,7 @@ inline int gemv_rows_for(mapi_storage st) {
     cfg.attrs = attr;                                                             \
     cfg.numAttrs = 1;                                                             \
     return cudaLaunchKernelEx(&cfg, k1_gemv_float<OP, ST, V, gemv_rows<ST>(), kWarps, \
-                                                  ((ST == kBF16 || ST == kFP8) ? kGemvCluster : 1)>, g); \
+                                                  kGemvCluster>, g);                              \
   }                                                                               \
   LaunchFn FNNAME(int op, int V) {                                                \
     switch (op * 16 + V) {                                                        \

@@ -132,7 +132,7 @@ struct mapi_ctx {
 
   // diagnostics
   bool prof_on = false;
-  // K1 may run in 8-CTA clusters on large BF16 / integer matrices; off for
+  // K1 may run in 8-CTA clusters on large matrices; off for
   // the serving loop, whose solves share the GPU with a persistent batched
   // launch (a cluster waits for eight free CTA slots at once)
   bool gemv_clusters = true;
