@@ -344,6 +344,26 @@ def test_switch_to_rpi_equals_the_two_phases(mapi_ctx, op):
     assert rel_l1(to_host(w), want) <= 1e-5
 
 
+@pytest.mark.parametrize("t1,t2", [(0, 30), (25, 0), (0, 0)])
+def test_switch_with_an_empty_phase(mapi_ctx, t1, t2):
+    """No MAPI steps: RPI from w0 at unit l2 norm; no RPI steps: MAPI's
+    iterate at unit l2 norm (Alg. 1 step 1 of the second phase)."""
+    n = 150
+    A = datagen.symmetric_gaussian(n, seed=65).astype(np.float32)
+    w0 = datagen.start_vector(n, seed=66)
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(A), "f32")
+    try:
+        w, it, _ = M.mapi_iterate_switch(mapi_ctx, mat, "min1", to_dev(w0), t1, t2)
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
+    Ad = A.astype(np.float64)
+    _, mid, it1, _ = oracle.mapi("min1", Ad, w0.astype(np.float64), t1)
+    _, want, it2, _ = oracle.mapi("dot", Ad, mid, t2)
+    assert it == [it1, it2] == [t1, t2]
+    assert rel_l1(to_host(w), want) <= 1e-5
+    assert abs(np.linalg.norm(to_host(w)) - 1.0) < 1e-5
+
+
 def test_switch_reaches_the_eigenvector(mapi_ctx):
     """The RPI phase converges to the dominant eigenvector; MAPI alone stops at
     a nearby pseudo-eigenvector."""
