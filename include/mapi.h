@@ -390,12 +390,13 @@ mapi_status mapi_get_stats(mapi_ctx* ctx, mapi_stats* out, int reset);
 
 /*
  * Batched MAPI: `count` independent instances, each a square packed matrix
- * with nvec start vectors, solved by Alg. 1 in two persistent launches:
- * instances with n >= 512 go to clusters of 8 CTAs (each CTA holds 1/8 of
- * the rows and the whole iterate, norms and deltas combined over the cluster
- * in a fixed order), the rest to single CTAs.  Clusters and CTAs claim whole
- * instances, largest first, and run all their steps; the nvec vectors of an
- * instance share every read of its matrix.  Same step,
+ * with nvec start vectors, solved by Alg. 1 in one persistent launch of
+ * 8-CTA clusters (replayed from a cached CUDA graph while the batch keeps its
+ * shape): instances with n >= 1024 take a whole cluster each (each CTA holds
+ * 1/8 of the rows and the whole iterate, norms and deltas combined over the
+ * cluster in a fixed order); once those are claimed, every CTA claims the
+ * smaller instances alone.  Claims go largest first and run all their steps;
+ * the nvec vectors of an instance share every read of its matrix.  Same step,
  * stop rule, flags and statuses as mapi_iterate, per vector.
  *   items     host array of count entries; every A is F32 (or every A is
  *             BF16), square, n <= 8192 / nvec (8192 for one vector, 2048

@@ -426,15 +426,22 @@ struct DeviceGuardB {
   }
 };
 
-mapi_status launch_batched(mapi_ctx* ctx, mapi_op op, mapi_storage st, int V, int r,
-                           const BatchArgs& args, cudaStream_t s, double args_bytes,
-                           double args_terms) {
-  BatchFn fn = batched_fn(op, st, V, r);
-  if (!fn) return fail(ctx, MAPI_EINVAL, "batched solve: op/storage/nvec not supported");
+struct BatchLaunch {
+  BatchFn fn = nullptr;
+  int nclusters = 0;
+};
+
+// Attributes and grid of one batched launch (host queries; before any
+// capture): as many 8-CTA clusters as fit, at most enough for the large
+// instances plus a CTA per small one.
+mapi_status plan_batched(mapi_ctx* ctx, mapi_op op, mapi_storage st, int V, int r,
+                         const BatchArgs& args, BatchLaunch* bl) {
+  bl->fn = batched_fn(op, st, V, r);
+  if (!bl->fn) return fail(ctx, MAPI_EINVAL, "batched solve: op/storage/nvec not supported");
   // whole iterate + a cluster rank's rows; the small phase uses 2 x kBatchLargeN x V
   static_assert(2 * kBatchLargeN * 4 <= kBatchIterFloats + kBatchRowFloats, "small phase");
   const size_t smem = sizeof(float) * (kBatchIterFloats + kBatchRowFloats);
-  MAPI_CUDA_TRY(ctx, cudaFuncSetAttribute((const void*)fn,
+  MAPI_CUDA_TRY(ctx, cudaFuncSetAttribute((const void*)bl->fn,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -444,20 +451,35 @@ mapi_status launch_batched(mapi_ctx* ctx, mapi_op op, mapi_storage st, int V, in
   attr[0].val.clusterDim.z = 1;
   cfg.blockDim = dim3(kBatchThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cfg.gridDim = dim3(kBatchCluster * ctx->sm_count, 1, 1);
   int nclusters = 0;
-  MAPI_CUDA_TRY(ctx, cudaOccupancyMaxActiveClusters(&nclusters, (const void*)fn, &cfg));
+  MAPI_CUDA_TRY(ctx, cudaOccupancyMaxActiveClusters(&nclusters, (const void*)bl->fn, &cfg));
   if (nclusters < 1) return fail(ctx, MAPI_ECUDA, "batched kernel does not fit");
-  // enough clusters for the large instances plus a CTA per small one
   const int want = args.nlarge + (args.count - args.nlarge + kBatchCluster - 1) / kBatchCluster;
-  nclusters = std::min(nclusters, std::max(1, want));
-  cfg.gridDim = dim3(kBatchCluster * nclusters, 1, 1);
+  bl->nclusters = std::min(nclusters, std::max(1, want));
+  return MAPI_OK;
+}
+
+// The claim counters' reset and the persistent launch, on stream s.
+mapi_status enqueue_batched(mapi_ctx* ctx, const BatchLaunch& bl, const BatchArgs& args,
+                            cudaStream_t s, double args_bytes, double args_terms) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kBatchCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kBatchThreads, 1, 1);
+  cfg.dynamicSmemBytes = sizeof(float) * (kBatchIterFloats + kBatchRowFloats);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(kBatchCluster * bl.nclusters, 1, 1);
   MAPI_CUDA_TRY(ctx, cudaMemsetAsync(args.next, 0, 64 * sizeof(int), s));
   cudaEvent_t ev = prof_begin(ctx, s);
-  MAPI_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, fn, args));
+  MAPI_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, bl.fn, args));
   prof_end(ctx, s, ev, MAPI_KC_BATCHED, args_bytes, args_terms);
   count_launch(ctx);
   return MAPI_OK;
@@ -472,7 +494,9 @@ namespace mapi {
 // last deltas come back in res ([iters, status] per vector) and dl.
 mapi_status batched_run(mapi_ctx* ctx, cudaStream_t stream, std::vector<BatchDev>& host,
                         mapi_op op, mapi_storage st, int V, std::vector<int>& res,
-                        std::vector<float>& dl) {
+                        std::vector<float>& dl, bool use_graph) {
+  // a cached graph is launched on the context's stream
+  use_graph = use_graph && stream == ctx->stream;
   const int count = (int)host.size();
   std::vector<int64_t> work(count);
   for (int i = 0; i < count; ++i) work[i] = (int64_t)host[i].n * host[i].n;
@@ -516,14 +540,37 @@ mapi_status batched_run(mapi_ctx* ctx, cudaStream_t stream, std::vector<BatchDev
     bytes += (double)work[i] * elem_bytes(st) * host[i].max_iters;
     terms += (double)work[i] * V * host[i].max_iters;
   }
-  if ((s = launch_batched(ctx, op, st, V, r > 0 ? r : 2, a, stream, bytes, terms)) != MAPI_OK)
-    return s;
+  BatchLaunch bl;
+  if ((s = plan_batched(ctx, op, st, V, r > 0 ? r : 2, a, &bl)) != MAPI_OK) return s;
+  GraphEntry* ge = nullptr;
+  if (use_graph) {
+    // the counters' reset and the persistent launch as one cached graph,
+    // replayed while the instance table keeps its shape (the table itself
+    // is copied in ahead of it on the same stream)
+    std::vector<int64_t> key = {3, (int64_t)op, (int64_t)st, V, r, count, nlarge,
+                                bl.nclusters, (int64_t)(uintptr_t)ctx->batch.p,
+                                (int64_t)ctx->prof_on};
+    if (ctx->prof_on) {  // the work counted per launch feeds only the profile
+      uint64_t bb, tb;
+      std::memcpy(&bb, &bytes, 8);
+      std::memcpy(&tb, &terms, 8);
+      key.push_back((int64_t)bb);
+      key.push_back((int64_t)tb);
+    }
+    s = launch_cached_graph(
+        ctx, key, [&](cudaStream_t cs) { return enqueue_batched(ctx, bl, a, cs, bytes, terms); },
+        &ge);
+  } else {
+    s = enqueue_batched(ctx, bl, a, stream, bytes, terms);
+  }
+  if (s != MAPI_OK) return s;
   res.assign(2 * V * count, 0);
   dl.assign(V * count, 0.f);
   MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(res.data(), d_res, res_b, cudaMemcpyDeviceToHost, stream));
   MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(dl.data(), d_dl, dl_b, cudaMemcpyDeviceToHost, stream));
   MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
-  prof_collect(ctx, ctx->pending, true);
+  if (ge) finish_graph(ctx, ge);
+  else prof_collect(ctx, ctx->pending, true);
   return MAPI_OK;
 }
 
@@ -570,7 +617,7 @@ extern "C" mapi_status mapi_iterate_batched(mapi_ctx* ctx, const mapi_batch_item
   }
   std::vector<int> res;
   std::vector<float> dl;
-  mapi_status s = batched_run(ctx, ctx->stream, host, op, st, V, res, dl);
+  mapi_status s = batched_run(ctx, ctx->stream, host, op, st, V, res, dl, true);
   if (s != MAPI_OK) return s;
   mapi_status result = MAPI_OK;
   for (int i = 0; i < count; ++i)

@@ -288,9 +288,10 @@ struct BatchDev {
 };
 // One persistent launch over the instances (all of storage st, nvec = V);
 // res gets [iters, status] per vector and dl the last deltas.  Synchronous.
+// With use_graph (and the context's stream) the launch is a cached CUDA graph.
 mapi_status batched_run(mapi_ctx* ctx, cudaStream_t stream, std::vector<BatchDev>& host,
                         mapi_op op, mapi_storage st, int V, std::vector<int>& res,
-                        std::vector<float>& dl);
+                        std::vector<float>& dl, bool use_graph = false);
 int batched_max_n(int nvec);
 
 // Serving loop (serve.cu): stops the loop and releases what it holds.
