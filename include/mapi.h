@@ -497,9 +497,11 @@ typedef struct {
  * the budget (mapi_config.hbm_budget_bytes; 0: 80 % of the device memory free
  * when the loop starts) and at most max_slots are resident.  It builds each
  * admitted request's matrix on the device (C, or G), keeps every iterate
- * resident, and advances all resident solves together: each round is one
- * persistent batched launch (as mapi_iterate_batched) of up to 25 steps per
- * solve, after which finished components are deflated or results copied out.
+ * resident, and advances all resident solves together: each round runs up
+ * to 25 steps of every solve, those with n < 2048 in one persistent batched
+ * launch per (storage, op) (as mapi_iterate_batched), larger ones through
+ * the GEMV of mapi_iterate on another stream at the same time; after it,
+ * finished components are deflated or results copied out.
  *   ticket   receives the request's handle (> 0).
  * Errors: MAPI_EINVAL (a field out of range, null pointer), MAPI_EBUDGET
  * (the request alone needs more device bytes than the budget: it could never
