@@ -1,7 +1,8 @@
 """Rank programs for the partitioned-algorithm tests: each runs on one gloo
 rank (CPU), computes its shard with the FP64 oracle and exchanges what the
 partition needs (an all-gather of y for row shards, an all-reduce of y for
-column shards, a gather of C tiles).  Rank 0 returns the assembled results.
+column shards, a gather of C tiles, an all-reduce of A_t for Alg. 3's
+sample shards).  Rank 0 returns the assembled results.
 """
 import numpy as np
 import torch
@@ -92,6 +93,29 @@ def instance_sharded_batch(rank, world, op, count, iters, seed):
     return [merged[i] for i in range(count)]
 
 
+def sample_sharded_minibatch(rank, world, op, N, D, T, s, beta, seed):
+    """Alg. 3 with each step's draws split over the ranks: every rank adds
+    the outer products x (+) x^T of its share, an all-reduce sums A_t, and
+    the rest of the step (v = A_t (+) w_t - beta w_{t-1}, both scaled by the
+    norm of v) runs alike on every rank."""
+    X = datagen.stochastic_pca_data(N, D, seed=seed).astype(np.float64)
+    batch = datagen.minibatches(N, T, s, seed=seed + 1)
+    w = datagen.start_vector(D, seed=seed + 2).astype(np.float64)
+    w = w / np.sqrt(np.sum(w * w))  # step 1
+    wp = np.zeros(D)
+    b, e = _split(s, world, rank)
+    for t in range(T):
+        idx = batch[t, b:e]
+        part = oracle.mincov(op, X[idx].T, 1.0) if e > b else np.zeros((D, D))
+        At = torch.from_numpy(np.ascontiguousarray(part))
+        dist.all_reduce(At)
+        A = At.numpy() / s
+        v = oracle.matvec(op, A, w) - beta * wp
+        L = np.sqrt(np.sum(v * v)) if op == "dot" else np.sum(np.abs(v))
+        wp, w = w / L, v / L
+    return w / np.sqrt(np.sum(w * w))
+
+
 def max_over_ranks_case(rank, world):
     """The benchmark's timing reduction on gloo: every rank reports its own
     time, all get the maximum."""
@@ -109,5 +133,7 @@ def run_all(rank, world):
         "mincov_min1": tiled_mincov(rank, world, "min1", 14, 90, 7),
         "mincov_min2": tiled_mincov(rank, world, "min2", 14, 90, 8),
         "batch_min1": instance_sharded_batch(rank, world, "min1", 7, 15, 9),
+        "mb_min1": sample_sharded_minibatch(rank, world, "min1", 500, 6, 8, 13, 0.2, 11),
+        "mb_dot": sample_sharded_minibatch(rank, world, "dot", 500, 6, 8, 13, 0.2, 12),
         "tmax": max_over_ranks_case(rank, world),
     }

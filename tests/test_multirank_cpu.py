@@ -1,7 +1,7 @@
 """The partitioned forms of the path on two gloo ranks (CPU): row-sharded
-Alg. 1, column-sharded pair step, tiled min-covariance and instance-sharded
-batches must reproduce the unsharded FP64 oracle; the benchmark's max-over-
-ranks timing reduction runs on the same ranks."""
+Alg. 1, column-sharded pair step, tiled min-covariance, instance-sharded
+batches and sample-sharded Alg. 3 must reproduce the unsharded FP64 oracle;
+the benchmark's max-over-ranks timing reduction runs on the same ranks."""
 import multiprocessing as mp
 import os
 import socket
@@ -85,6 +85,18 @@ def test_instance_sharded_batch_equals_unsharded(ranks):
         A = datagen.wishart_instance(int(sizes[i]), seed=9 + i).astype(np.float64)
         w0 = datagen.start_vector(int(sizes[i]), seed=9 + 100 + i).astype(np.float64)
         np.testing.assert_array_equal(got, oracle.mapi("min1", A, w0, 15)[1])
+
+
+@pytest.mark.parametrize("op,seed", [("min1", 11), ("dot", 12)])
+def test_sample_sharded_minibatch_equals_unsharded(ranks, op, seed):
+    """Alg. 3 with every step's 13 draws split 7 / 6 over the ranks."""
+    X = datagen.stochastic_pca_data(500, 6, seed=seed).astype(np.float64)
+    batch = datagen.minibatches(500, 8, 13, seed=seed + 1)
+    w0 = datagen.start_vector(6, seed=seed + 2).astype(np.float64)
+    st, want = oracle.minibatch_momentum(op, X, batch, 0.2, w0)
+    assert st == oracle.OK
+    for r in range(WORLD):
+        np.testing.assert_allclose(ranks[r][f"mb_{op}"], want, rtol=1e-11, atol=1e-13)
 
 
 def test_max_over_ranks(ranks):
