@@ -34,6 +34,7 @@ __all__ = [
     "start_vectors",
     "symmetric_gaussian",
     "spiked_pca_data",
+    "spiked_pca_basis",
     "barabasi_albert_digraph",
     "wishart_sizes",
     "wishart_instance",
@@ -103,6 +104,15 @@ def spiked_pca_data(D: int, N: int, seed: int = 0,
     X[mask] = r.laplace(0.0, laplace_scale, size=cnt)
     X -= X.mean(axis=1, keepdims=True)
     return np.ascontiguousarray(X.astype(dtype))
+
+
+def spiked_pca_basis(D: int, seed: int = 0, spikes=DEFAULT_SPIKES) -> np.ndarray:
+    """The orthonormal D x k basis U that ``spiked_pca_data`` plants with the
+    same seed (its first draw), for tests that start an iteration near the
+    planted directions."""
+    k = min(len(spikes), D)
+    q, _ = np.linalg.qr(rng(seed).standard_normal((D, k)))
+    return q
 
 
 def barabasi_albert_digraph(n: int, m: int = 8, seed: int = 0):

@@ -130,6 +130,88 @@ def test_pair_step_full_size(mapi_ctx):
         M.mapi_matrix_free(mapi_ctx, mat)
 
 
+def _pair_topk_parity(ctx, X, Xs, k, op, T, W0, st="f32"):
+    """Pair-mode top-k on the GPU against the oracle on the stored values Xs:
+    the same status, the same steps per component, and every component
+    finished before a stop within TOL32."""
+    D, N = X.shape
+    mat = M.mapi_matrix_upload(ctx, to_dev(X), st)
+    try:
+        ost, Po, oits = oracle.pca_topk("pair", op, Xs, k, T, float(N), W0.T)
+        try:
+            P, its = M.mapi_pca_topk(ctx, mat, k, "pair", op, T, float(N), to_dev(W0))
+            gst = 0
+        except M.MapiError as e:
+            (P, its), gst = e.partial, e.status
+        assert gst == ost and its == list(oits), (gst, ost, its, list(oits))
+        P = to_host(P)
+        first_stop = next((c for c in range(k) if oits[c] < T), k) if ost else k
+        errs = [rel_l1(P[c], Po[:, c]) for c in range(first_stop)]
+        for c, err in enumerate(errs):
+            assert err <= TOL32, (c, err, errs)
+        return first_stop, errs
+    finally:
+        M.mapi_matrix_free(ctx, mat)
+
+
+@pytest.mark.parametrize("op", ["min1", "min2"])
+@pytest.mark.parametrize("st", ["f32", "bf16"])
+def test_pair_mode_top8_every_deflation_slot(mapi_ctx, op, st):
+    """D = 1024, the largest pair-mode order, and k = 8 as in the PCA
+    workload: components 2..8 deflate their iterate by 1..7 earlier outer
+    products (Alg. 2 step 6 with the sum form of §1).  The epilogue gives
+    earlier component m to CTA rank m mod 4 of the last cluster and, within
+    it, to warp group m div 4, so this covers all four ranks of both groups."""
+    D, N, k, T = 1024, 8192, 8, 12
+    X = spiked(D, N, seed=51)
+    W0 = np.stack([datagen.start_vector(D, seed=510 + c) for c in range(k)])
+    Xs = X.astype(np.float64) if st == "f32" else oracle.quant_bf16(X)
+    done, _ = _pair_topk_parity(mapi_ctx, X, Xs, k, op, T, W0, st)
+    if op == "min1":
+        assert done == k  # min1 never stops on a zero norm here
+
+
+@pytest.mark.parametrize("op", ["min1", "min2", "dot"])
+@pytest.mark.parametrize("k", [12, 20])
+def test_pair_mode_more_components_than_epilogue_slots(mapi_ctx, op, k):
+    """k = 12 and 20: earlier components beyond the eight the epilogue holds
+    at once (m >= 8) are loaded again by the warp group that owns them, up to
+    three components per group."""
+    D, N, T = 64, 2000, 10
+    X = spiked(D, N, seed=61 + k)
+    W0 = np.stack([datagen.start_vector(D, seed=610 + c) for c in range(k)])
+    done, _ = _pair_topk_parity(mapi_ctx, X, X.astype(np.float64), k, op, T, W0)
+    if op != "min2":
+        assert done == k
+
+
+def test_pair_step_full_size_all_deflation_slots(mapi_ctx):
+    """D = 1024, N = 65536 (the PCA workload), k = 8 with one step per
+    component: component c (c = 1..8) makes one pair step from its start and
+    deflates it by the GPU's own components 1..c-1, so the oracle is fed the
+    same earlier components and compared one step at a time.  The starts are
+    the planted directions, so the components are well separated."""
+    D, N, k = 1024, 65536, 8
+    X = spiked(D, N, seed=0)
+    U = datagen.spiked_pca_basis(D, seed=0)
+    W0 = np.ascontiguousarray(U[:, :k].T.astype(np.float32))
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(X), "f32")
+    try:
+        P, its = M.mapi_pca_topk(mapi_ctx, mat, k, "pair", "min1", 1, float(N), to_dev(W0))
+        assert its == [1] * k
+        P = to_host(P)
+        for c in range(k):
+            w = W0[c].astype(np.float64)
+            y = oracle.pair_step("min1", X, w / np.linalg.norm(w), float(N))
+            if c:
+                y = oracle.deflate_vec("min1", y, P[:c].T)
+            want = y / np.abs(y).sum()
+            want /= np.linalg.norm(want)
+            assert rel_l1(P[c], want) <= TOL32, c
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
+
+
 def test_pca_bad_arguments(mapi_ctx):
     X = spiked(16, 64, seed=1)
     mat = M.mapi_matrix_upload(mapi_ctx, to_dev(X), "f32")
