@@ -26,7 +26,8 @@ __all__ = [
     "mapi_get_stats", "mapi_iterate_noalloc", "mapi_iterate_batched",
     "mapi_autotune_batched", "mapi_submit", "mapi_poll", "mapi_cancel",
     "mapi_pagerank_sparse", "mapi_iterate_switch", "mapi_minibatch_momentum",
-    "mapi_mavp_project", "mapi_image_reconstruct", "KERNEL_CLASSES",
+    "mapi_mavp_project", "mapi_image_reconstruct", "mapi_pair_phases", "mapi_debug_stall",
+    "KERNEL_CLASSES",
     "OP", "ST", "FLAG_FINAL_L2", "FLAG_RAW_START", "SCALE_AUTO",
     "PCA_MINCOV", "PCA_PAIR", "STATUS",
 ]
@@ -119,6 +120,8 @@ def load(path: str | None = None):
         "mapi_pagerank": [p_, p_, p_, i, d, i, i, p_, i, d, p_, p_, p_],
         "mapi_pagerank_sparse": [p_, p_, p_, i, d, i, p_, i, d, p_, p_, p_],
         "mapi_profile": [p_, i],
+        "mapi_pair_phases": [p_, i, p_],
+        "mapi_debug_stall": [p_, i64],
         "mapi_get_stats": [p_, C.POINTER(_Stats), i],
         "mapi_iterate_noalloc": [p_, i, i64, i, p_, i, d, u, p_, p_, p_, p_],
         "mapi_iterate_batched": [p_, p_, i, i, i, i, d, u, p_, p_, p_],
@@ -429,6 +432,24 @@ def mapi_profile(ctx, enable: bool = True) -> None:
     _check(load().mapi_profile(ctx, 1 if enable else 0), "mapi_profile", ctx)
 
 
+PAIR_PHASES = ("steps", "gap_to_start", "start_to_first_loop_end", "start_to_last_loop_end",
+               "last_loop_end_to_elected", "reduce_partials", "deflate", "norm_and_stop")
+
+
+def mapi_pair_phases(ctx, enable: bool = True) -> dict:
+    """Pair-step phase stamps since stamping was last switched on (steps,
+    then microseconds per step for each phase); then switch it on or off."""
+    out = (C.c_double * 8)()
+    _check(load().mapi_pair_phases(ctx, 1 if enable else 0, out), "mapi_pair_phases", ctx)
+    return {k: float(v) for k, v in zip(PAIR_PHASES, out)}
+
+
+def mapi_debug_stall(ctx, limit_ns: int) -> None:
+    """Failure-detection test hook: later pair steps also wait, bounded by
+    limit_ns, on a barrier that nothing arrives at (0 turns it off)."""
+    _check(load().mapi_debug_stall(ctx, int(limit_ns)), "mapi_debug_stall", ctx)
+
+
 def mapi_get_stats(ctx, reset: bool = False) -> dict:
     """Launch count and, per kernel class, timed launches, summed ms,
     algorithmic bytes and terms."""
@@ -448,9 +469,27 @@ def mapi_iterate_noalloc(A, op, w0, max_iters: int, tol_l1: float = 0.0, flags: 
     CUDA float32 (n, >= n) with rows 16-byte aligned; w0: (n,).  w_out must be
     preallocated by callers that cannot allocate.  Returns (w_out, iters, delta)."""
     torch = _torch()
-    n = A.shape[0]
+    # every size, type and device is checked here, before the library runs:
+    # the C side cannot see how long w0 and w_out are, and a short or
+    # half-precision w_out would be written past its end
     if A.dim() != 2 or A.stride(1) != 1 or A.dtype != torch.float32:
         raise ValueError("A must be a 2-D float32 tensor with contiguous rows")
+    n = A.shape[0]
+    if A.shape[1] < n:
+        raise ValueError(f"A must hold n = {n} columns, has {A.shape[1]}")
+    for name, v in (("w0", w0), ("w_out", w_out)):
+        if v is None:
+            continue
+        if v.dtype != torch.float32 or v.numel() != n or (v.dim() > 1 and not v.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float32 tensor of {n} elements")
+    if not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor")
+    dev = A.device
+    if dev.index != torch.cuda.current_device():
+        raise ValueError("A must be on the current CUDA device")
+    for name, v in (("w0", w0), ("w_out", w_out)):
+        if v is not None and v.device != dev:
+            raise ValueError(f"{name} must be on {dev}, the device of A")
     if w_out is None:
         w_out = torch.empty(n, dtype=torch.float32, device=A.device)
     opi = OP[op] if isinstance(op, str) else int(op)
