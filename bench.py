@@ -282,6 +282,22 @@ def run_gpu(args, rank, world, local_rank, dist):
     return line
 
 
+def pair_phases(M, ctx, Xd, W0d, P, storage="f32"):
+    """Where the time of a pair step goes: the headline solve run once with
+    the kernel's %globaltimer phase stamps on (microseconds per step,
+    averaged over its 800 steps).  The stamps add a few atomics per CTA."""
+    mat = M.mapi_matrix_upload(ctx, Xd, storage)
+    try:
+        M.mapi_pair_phases(ctx, True)
+        M.mapi_pca_topk(ctx, mat, K_COMP, "pair", "min1", ITERS, float(N), W0d, P_out=P)
+        M.mapi_pair_phases(ctx, True)  # the first run captured the graph: start again
+        M.mapi_pca_topk(ctx, mat, K_COMP, "pair", "min1", ITERS, float(N), W0d, P_out=P)
+        ph = M.mapi_pair_phases(ctx, False)
+    finally:
+        M.mapi_matrix_free(ctx, mat)
+    return {k: round(v, 3) for k, v in ph.items()}
+
+
 def alu_peak_terms(sm_mhz: float = 2070.0, sms: int = 152) -> float:
     """ALU roofline of the float MAVP term: each term needs two min/max
     instructions on the ALU pipe, which issues 64 lanes per clock per SM
@@ -331,6 +347,7 @@ def run_variants(M, ctx, torch, dev, X, W0d, peaks):
             M.mapi_matrix_free(ctx, mat)
         return ms, st
 
+    out["pca_pair_f32_phases_us"] = pair_phases(M, ctx, Xd, W0d, P)
     ms, st = pca("bf16", "pair")
     pr = st["pair"]
     gbs = pr["bytes"] / (pr["ms"] / 1e3) / 1e9
@@ -420,10 +437,70 @@ def run_variants(M, ctx, torch, dev, X, W0d, peaks):
         "row_step_hbm_frac": round(gv["bytes"] / (gv["ms"] / 1e3) / 1e9 / hbm, 4)
         if gv["ms"] else None,
         "algorithmic_bytes_per_row_step": 16 * nnz + 8 * n}
+    out["rpi_plain_gemv"] = run_rpi_gemv(torch, dev, hbm, Xd)
     out["image_reconstruct_128"] = run_image(M, ctx, torch, dev, hbm)
     out["minibatch_momentum_1e6x10"] = run_minibatch(M, ctx, torch, dev)
     out["serve_mixed"] = run_serving(M, torch, dev)
     return out
+
+
+def run_rpi_gemv(torch, dev, hbm, Xd):
+    """The comparison baseline: regular power iteration (Eq. (1)) through a
+    plain vendor GEMV (torch.mv, i.e. cuBLAS) on the same matrices, with the
+    same number of steps.  Not the product path: it only shows how the MAVP
+    kernels compare with a library GEMV that streams the same bytes.
+      * PageRank: the dense n = 16384 Google matrix (Eq. (11), formed here
+        with torch), b <- G b / ||G b||_2, FP32 and BF16;
+      * pair PCA: b <- X (X^T b) / N / ||.||_2 on the D = 1024 x N = 65536 X,
+        two GEMVs (two reads of X) per step, FP32 and BF16."""
+    import datagen
+    res = {}
+    n, alpha, T = 16384, 0.85, 100
+    ip, ix = datagen.barabasi_albert_digraph(n, m=8, seed=0)
+    ipd = torch.from_numpy(ip.astype(np.int64)).to(dev)
+    ixd = torch.from_numpy(ix.astype(np.int64)).to(dev)
+    deg = ipd[1:] - ipd[:-1]
+    src = torch.repeat_interleave(torch.arange(n, device=dev), deg)
+    G = torch.full((n, n), (1.0 - alpha) / n, dtype=torch.float32, device=dev)
+    G.index_put_((ixd, src), (alpha / deg[src].to(torch.float64)).to(torch.float32),
+                 accumulate=True)
+    dang = torch.nonzero(deg == 0).flatten()
+    G[:, dang] += alpha / n
+    w0 = torch.from_numpy(datagen.start_vector(n, seed=0, low=0.0, high=1.0)).to(dev)
+
+    def rpi(mv, b, steps):
+        for _ in range(steps):
+            y = mv(b)
+            b = y / torch.linalg.vector_norm(y)
+        return b
+
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        Gt = G.to(dt)
+        b0 = (w0 / torch.linalg.vector_norm(w0)).to(dt)
+        ms = timed(torch, lambda: rpi(lambda b: torch.mv(Gt, b), b0, T), 2)
+        gms = timed(torch, lambda: [torch.mv(Gt, b0) for _ in range(T)], 2)
+        eb = Gt.element_size()
+        gbs = n * n * eb / (gms / T / 1e3) / 1e9
+        res[f"pagerank_n16384_{name}"] = {
+            "iters_per_s": round(T / (ms / 1e3), 1), "us_per_iter": round(ms / T * 1e3, 2),
+            "gemv_us": round(gms / T * 1e3, 2), "gemv_gbs": round(gbs, 1),
+            "hbm_frac": round(gbs / hbm, 4)}
+        del Gt
+    del G
+    Dd, Nn = Xd.shape
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        Xt = Xd.to(dt)
+        b0 = torch.ones(Dd, dtype=dt, device=dev) / float(np.sqrt(Dd))
+        step = lambda b: torch.mv(Xt, torch.mv(Xt.t(), b)) / Nn
+        ms = timed(torch, lambda: rpi(step, b0, T), 2)
+        gbs = 2.0 * Dd * Nn * Xt.element_size() / (ms / T / 1e3) / 1e9
+        res[f"pca_pair_d1024_n65536_{name}"] = {
+            "iters_per_s": round(T / (ms / 1e3), 1), "us_per_iter": round(ms / T * 1e3, 2),
+            "gbs_two_reads_of_X": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+        del Xt
+    res["note"] = ("torch.mv (cuBLAS GEMV) RPI with l2 normalisation; pair PCA reads X twice "
+                   "per step (X^T b, then X t), the MAVP pair kernel once")
+    return res
 
 
 def psnr(a, b) -> float:
@@ -710,7 +787,14 @@ def run_case(case: str):
     from paper_2110_12065_gb300 import build as B
     B.build()
     ctx = M.mapi_create(0)
-    if case in ("pair-f32", "pair-bf16", "mincov-f32", "mincov-bf16"):
+    if case in ("pair-phases", "pair-phases-bf16"):
+        X, W0 = make_inputs(0)
+        W0d = torch.from_numpy(W0).cuda()
+        P = torch.empty_like(W0d)
+        ph = pair_phases(M, ctx, torch.from_numpy(X).cuda(), W0d, P,
+                         "bf16" if case.endswith("bf16") else "f32")
+        out = json.dumps({"case": case, "us_per_step": ph})
+    elif case in ("pair-f32", "pair-bf16", "mincov-f32", "mincov-bf16"):
         mode, st = case.split("-")
         X = datagen.spiked_pca_data(D, N, seed=0)
         mat = M.mapi_matrix_upload(ctx, torch.from_numpy(X).cuda(), st)
@@ -781,7 +865,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--case", default=None,
                     help="run one short solve of a workload for a profiler and exit: "
-                         "pair-f32, pair-bf16, mincov-f32, mincov-bf16, pagerank-f32, "
+                         "pair-f32, pair-bf16, pair-phases, pair-phases-bf16, "
+                         "mincov-f32, mincov-bf16, pagerank-f32, "
                          "pagerank-bf16, pagerank-fp8, pagerank-i16, pagerank-sparse, batched-f32, serve, "
                          "image, minibatch")
     args = ap.parse_args()

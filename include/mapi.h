@@ -386,6 +386,30 @@ mapi_status mapi_profile(mapi_ctx* ctx, int enable);
 /* Copy the counters to *out (may be NULL) and, if reset != 0, zero them. */
 mapi_status mapi_get_stats(mapi_ctx* ctx, mapi_stats* out, int reset);
 
+/* Phase time stamps of the pair step (the PCA pair mode of mapi_pca_topk).
+ * Synchronises ctx's stream, then writes to out_us (8 doubles, may be NULL)
+ * what was stamped since stamping was last switched on: [0] the steps
+ * stamped, then per step, in microseconds of %globaltimer: [1] from the end
+ * of the previous step's epilogue to the earliest start of this step's CTAs
+ * (after the programmatic-dependency wait), [2] from that start to the first
+ * CTA's end of its tile loop, [3] to the last CTA's, [4] from the last loop
+ * end to the election of the epilogue cluster, [5] the reduction of the
+ * cluster partials, [6] the deflation, [7] norm, normalisation and stop
+ * test.  enable != 0 then clears the stamps and stamps later pair steps;
+ * enable == 0 stops.  A few global atomics per CTA and step while on.
+ * Not part of the method: it shows where a step's time goes. */
+mapi_status mapi_pair_phases(mapi_ctx* ctx, int enable, double* out_us);
+
+/* Failure-detection test hook.  limit_ns > 0: in every later pair step each
+ * CTA also waits, through the same bounded wait as its tile copies and
+ * cluster exchanges, on a barrier that nothing ever arrives at, with this
+ * limit (at most 2 s).  No copy or store is pending on that barrier, so the
+ * wait just runs out; the step then completes as usual and reports the
+ * expiry like any other bounded wait, so the solve stops with
+ * MAPI_ETIMEOUT and the context stays usable.  0 (the default) turns it
+ * off.  MAPI_EINVAL for a negative or larger limit. */
+mapi_status mapi_debug_stall(mapi_ctx* ctx, int64_t limit_ns);
+
 
 
 /*
@@ -544,13 +568,18 @@ mapi_status mapi_cancel(mapi_ctx* ctx, uint64_t ticket);
  *   w_out  device, n FP32 (caller-owned): the last iterate.
  *   iters_done, last_delta: host scalars (may be NULL).
  * Limit: n <= 8192; a larger n (or a bad pointer, lda or op) returns
- * MAPI_EINVAL before anything runs.
+ * MAPI_EINVAL before anything runs.  The library cannot see the lengths of
+ * w0 and w_out: they must hold n floats (the Python binding checks this).
+ * Cost: the call enqueues all max_iters step kernels up front, whatever step
+ * the stop rule fires at; the steps after it return at once but are still
+ * launched, so a large max_iters with an early stop pays for those launches.
  * Scratch: one static device array of about 320 KiB inside the library,
  * present on every GPU that loads it until the process exits.  The first
- * call on a device looks its address up (cudaGetSymbolAddress); make that
- * first call before any stream capture.  Every call reuses the same array
- * and rewrites what it needs, so calls that overlap on the GPU (other
- * threads, other streams) race with each other: serialise them.
+ * call on a device looks the array's address up (cudaGetSymbolAddress), so
+ * make that first call before any stream capture begins.  Every call
+ * reuses the same array and rewrites what it needs, so calls that overlap on
+ * the GPU (other threads, other streams) race with each other: serialise
+ * them.
  */
 mapi_status mapi_iterate_noalloc(const float* A, int n, int64_t lda, mapi_op op,
                                  const float* w0, int max_iters, double tol_l1,

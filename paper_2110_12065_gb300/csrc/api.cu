@@ -386,7 +386,7 @@ mapi_status mapi_destroy(mapi_ctx* ctx) {
   for (auto* m : ms) free_matrix(ctx, m);
   for (DevBuf* b : {&ctx->ypart, &ctx->wbuf0, &ctx->wbuf1, &ctx->ctl, &ctx->aux, &ctx->mcpart,
                     &ctx->pca_c0, &ctx->pca_c1, &ctx->pca_q, &ctx->pca_defl, &ctx->batch,
-                    &ctx->hyb, &ctx->outer, &ctx->img})
+                    &ctx->hyb, &ctx->outer, &ctx->img, &ctx->pair_phases})
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
@@ -686,6 +686,39 @@ mapi_status mapi_pagerank(mapi_ctx* ctx, const int* indptr, const int* indices, 
 mapi_status mapi_profile(mapi_ctx* ctx, int enable) {
   if (!ctx) return MAPI_EINVAL;
   ctx->prof_on = enable != 0;
+  return MAPI_OK;
+}
+
+mapi_status mapi_pair_phases(mapi_ctx* ctx, int enable, double* out_us) {
+  if (!ctx) return MAPI_EINVAL;
+  DeviceGuard g(ctx->device);
+  MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (out_us) {
+    for (int i = 0; i < 8; ++i) out_us[i] = 0.0;
+    if (ctx->pair_phases.p) {
+      PairPhases h;
+      MAPI_CUDA_TRY(ctx, cudaMemcpy(&h, ctx->pair_phases.p, sizeof(h), cudaMemcpyDeviceToHost));
+      const double n = (double)h.sum[7];
+      out_us[0] = n;
+      if (n > 0)
+        for (int i = 0; i < 7; ++i) out_us[1 + i] = (double)h.sum[i] / n / 1e3;
+    }
+  }
+  if (enable) {
+    mapi_status st = ensure(ctx, ctx->pair_phases, sizeof(PairPhases));
+    if (st != MAPI_OK) return st;
+    PairPhases h{};
+    h.start_min = ~0ull;
+    h.loop_min = ~0ull;
+    MAPI_CUDA_TRY(ctx, cudaMemcpy(ctx->pair_phases.p, &h, sizeof(h), cudaMemcpyHostToDevice));
+  }
+  ctx->phases_on = enable != 0;
+  return MAPI_OK;
+}
+
+mapi_status mapi_debug_stall(mapi_ctx* ctx, int64_t limit_ns) {
+  if (!ctx || limit_ns < 0 || limit_ns > 2000000000LL) return MAPI_EINVAL;
+  ctx->stall_ns = (long long)limit_ns;
   return MAPI_OK;
 }
 

@@ -227,7 +227,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                : "memory");
 }
 // Bounded wait on an mbarrier phase; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity,
+                                          long long limit_ns = kWaitLimitNs) {
   const uint32_t a = smem_u32(bar);
   long long t0 = 0;
   for (int i = 0;; ++i) {
@@ -240,7 +241,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     if (ok) return true;
     if (i == 0) t0 = globaltimer_ns();
-    else if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    else if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
 __device__ __forceinline__ uint32_t mapa_u32(uint32_t local, unsigned rank) {
@@ -349,6 +350,35 @@ struct Kahan {
     s = t;
   }
   __device__ __forceinline__ float value() const { return s - c; }
+};
+
+// Compensated sum as an unevaluated pair hi + lo: every addition is made
+// exact by Knuth's two-sum (the rounding error of hi + x is recovered and
+// added into lo), and a product enters with its own rounding error
+// recovered by a fused multiply-add.  The operations are written with the
+// explicitly rounded intrinsics so that the compiler cannot fuse or reorder
+// them.
+struct TwoSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  // hi + lo += a * b
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -p);
+    add(p);
+    lo = __fadd_rn(lo, pe);
+  }
+  __device__ __forceinline__ void add(const TwoSum& o) {
+    add(o.hi);
+    lo = __fadd_rn(lo, o.lo);
+  }
+  __device__ __forceinline__ float value() const { return __fadd_rn(hi, lo); }
 };
 
 // Deterministic block sum (fixed butterfly order); every thread gets the

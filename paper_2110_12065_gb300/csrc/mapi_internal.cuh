@@ -100,6 +100,21 @@ namespace mapi {
 struct Server;
 }
 
+namespace mapi {
+// Time stamps of pair steps (%globaltimer, ns), filled while phase stamping
+// is on: the earliest start of the current step's CTAs (after the
+// dependency wait), the earliest and latest end of a CTA's tile loop, the
+// end of the previous step, and per phase the nanoseconds summed over the
+// steps: [0] previous end -> start, [1] start -> first loop end, [2] start
+// -> last loop end, [3] last loop end -> epilogue elected, [4] reduction of
+// the cluster partials, [5] deflation, [6] norm, normalisation and stop
+// test, [7] steps stamped.
+struct PairPhases {
+  unsigned long long start_min, loop_min, loop_max, prev_end;
+  unsigned long long sum[8];
+};
+}  // namespace mapi
+
 struct mapi_ctx {
   int device = 0;
   int sm_count = 0;
@@ -132,6 +147,9 @@ struct mapi_ctx {
 
   // diagnostics
   bool prof_on = false;
+  bool phases_on = false;      // stamp the phases of pair steps
+  DevBuf pair_phases;          // one mapi::PairPhases
+  long long stall_ns = 0;      // > 0: fault-detection test of the bounded waits
   // K1 may run in 8-CTA clusters on large matrices; off for
   // the serving loop, whose solves share the GPU with a persistent batched
   // launch (a cluster waits for eight free CTA slots at once)

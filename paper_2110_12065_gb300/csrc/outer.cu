@@ -272,18 +272,25 @@ __global__ void __launch_bounds__(256)
 // Alg. 2 steps 1-3 for N images of P pixels (row i = image i): m_p = mean
 // over the images (in image order), X[p][i] = v_i[p] - m_p packed (P rows,
 // N columns, zero padding up to ld), Z[i][p] the same values row-wise.
+// The mean is formed by a compensated (two-sum) addition and kept as the
+// unevaluated pair m_hi + m_lo, and each centred value is (v - m_hi) - m_lo,
+// so a pixel that every image shares centres to exactly 0 (a plain FP32
+// mean would leave +-1 ulp there, where the exact centring has zeros) and
+// every other value is rounded about once.
 __global__ void k_image_center(const float* __restrict__ img, int N, int P, int64_t ld,
                                float* __restrict__ X, float* __restrict__ Z,
                                float* __restrict__ mean) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  float s = 0.f;
-  for (int i = 0; i < N; ++i) s += img[(int64_t)i * P + p];
-  const float m = s / (float)N;
-  mean[p] = m;
+  TwoSum s;
+  for (int i = 0; i < N; ++i) s.add(img[(int64_t)i * P + p]);
+  const float fN = (float)N;
+  const float mh = s.value() / fN;
+  const float ml = (fmaf(-mh, fN, s.hi) + s.lo) / fN;
+  mean[p] = mh + ml;
   float* xr = X + (int64_t)p * ld;
   for (int i = 0; i < N; ++i) {
-    const float v = img[(int64_t)i * P + p] - m;
+    const float v = (img[(int64_t)i * P + p] - mh) - ml;
     xr[i] = v;
     Z[(int64_t)i * P + p] = v;
   }

@@ -280,7 +280,15 @@ struct PairArgs {
                   // step starts on the tiles the previous one read last and
                   // that are still in L2
   int keep_tiles; // this many of a cluster's last tiles are kept in L2
+  long long stall_ns;  // > 0: fault-detection test, see k_pair_partial
+  PairPhases* phases;  // non-null: time stamps of the step's phases
 };
+
+// The phase stamps (%globaltimer, ns) of pair steps, summed over the steps
+// that ran: a diagnostic of where a step's time goes.
+__device__ __forceinline__ unsigned long long gtimer_u64() {
+  return (unsigned long long)globaltimer_ns();
+}
 
 // Floats of shared memory the last cluster's epilogue needs: ys, u, wo (own
 // rows), yfull and cbuf (D_pad each), four scan buffers and the component's
@@ -366,6 +374,9 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
       }
     }
   };
+  const bool stamp = a.phases && r == 0 && threadIdx.x == 0;
+  unsigned long long t_elect = 0, t_reduce = 0, t_defl = 0;
+  if (stamp) t_elect = gtimer_u64();
   // 0. prefetch: the first component of each deflating warp
   if (r + CS * h < a.defl.nprev) load_comp(r + CS * h, h, th, kEpiHalf);
   // 1. own rows of y: one row per thread; the row's cluster partials are all
@@ -391,6 +402,7 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
     ys[i] = d < D ? sum / a.denom : 0.f;
   }
   __syncthreads();
+  if (stamp) t_reduce = gtimer_u64();
   // 2. deflation
   if (a.defl.nprev > 0) {
     cluster.sync();
@@ -403,15 +415,18 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
     {
       // group g = warps 4g .. 4g + 3 deflates component r + CS g (and every
       // 2 CS-th after it); warp wq of the group scans sorted positions
-      // [256 wq, 256 wq + 256), eight per lane
+      // [256 wq, 256 wq + 256), eight per lane.  Every sum is compensated
+      // (TwoSum: hi + lo): the lane's eight terms, the scan over the lanes,
+      // the warps' offsets; each prefix A_p = sum_{q <= p} c_q z_q and each
+      // suffix S_p = sum_{q > p} z_q is rounded once, when it is stored.
       const int g = warp >> 2, wq = warp & 3, tg = threadIdx.x & 127;
-      __shared__ float gtot[2][4][4];
+      __shared__ float gtot[2][4][8];
       float* cb = cbuf + g * a.D_pad;
       float* sA = arrays(g);
-      float* sB = sA + kDeflPadded;
-      float* sA2 = sB + kDeflPadded;
-      float* sB2 = sA2 + kDeflPadded;
-      const float* wm_s = sB2 + kDeflPadded;
+      float* sS = sA + kDeflPadded;
+      float* sA2 = sS + kDeflPadded;
+      float* sS2 = sA2 + kDeflPadded;
+      const float* wm_s = sS2 + kDeflPadded;
       const float* cs_s = wm_s + kDeflPadded;
       const int* perm_s = reinterpret_cast<const int*>(cs_s + kDeflPadded);
       const int* ub_s = perm_s + kDeflPadded;
@@ -423,20 +438,39 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
         }
         group_bar(g);
         if (dot) {
-          float pd = 0.f;
-          for (int i = tg; i < D; i += 128) pd += wm_s[i] * yfull[i];
+          TwoSum pd;
+          for (int i = tg; i < D; i += 128) pd.add_prod(wm_s[i], yfull[i]);
 #pragma unroll
-          for (int o = 16; o; o >>= 1) pd += __shfl_xor_sync(0xffffffffu, pd, o);
-          if (lane == 0) gtot[g][wq][0] = pd;
+          for (int o = 16; o; o >>= 1) {
+            TwoSum q;
+            q.hi = __shfl_xor_sync(0xffffffffu, pd.hi, o);
+            q.lo = __shfl_xor_sync(0xffffffffu, pd.lo, o);
+            pd.add(q);
+          }
+          if (lane == 0) {
+            gtot[g][wq][0] = pd.hi;
+            gtot[g][wq][1] = pd.lo;
+          }
           group_bar(g);
-          const float dv = gtot[g][0][0] + gtot[g][1][0] + gtot[g][2][0] + gtot[g][3][0];
-          for (int i = tg; i < D; i += 128) cb[i] += wm_s[i] * dv;
+          TwoSum dv;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            TwoSum e;
+            e.hi = gtot[g][q][0];
+            e.lo = gtot[g][q][1];
+            dv.add(e);
+          }
+          const float d = dv.value();
+          for (int i = tg; i < D; i += 128) cb[i] = fmaf(wm_s[i], d, cb[i]);
           group_bar(g);
           continue;
         }
-        // running sums over this lane's 8 positions
-        float ra = 0.f, rb = 0.f, ra2 = 0.f, rb2 = 0.f;
+        // sorted position p contributes c z to A and z to B (z = s y, with
+        // c and s the magnitude and sign of the component there) and, for
+        // min2, c y and y
         const int p0 = wq * 256 + lane * 8;
+        // 1. this lane's totals
+        TwoSum la, lb, la2, lb2;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int p = p0 + k;
@@ -445,74 +479,110 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
             const float y = yfull[i];
             const float c = cs_s[dpad(p)];
             const float z = sgnf(wm_s[i]) * y;
-            ra += c * z;
-            rb += z;
+            la.add_prod(c, z);
+            lb.add(z);
             if (two) {
-              ra2 += c * y;
-              rb2 += y;
+              la2.add_prod(c, y);
+              lb2.add(y);
             }
           }
-          sA[dpad(p)] = ra;
-          sB[dpad(p)] = rb;
-          if (two) {
-            sA2[dpad(p)] = ra2;
-            sB2[dpad(p)] = rb2;
-          }
         }
-        // lane offsets within the warp, then warp offsets within the group
-        float oa = ra, ob = rb, oa2 = ra2, ob2 = rb2;
+        // 2. inclusive scan of the lane totals over the warp
+        TwoSum ia = la, ib = lb, ia2 = la2, ib2 = lb2;
+        auto up = [&](TwoSum& v, int o) {
+          TwoSum n;
+          n.hi = __shfl_up_sync(0xffffffffu, v.hi, o);
+          n.lo = __shfl_up_sync(0xffffffffu, v.lo, o);
+          if (lane >= o) v.add(n);
+        };
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const float na = __shfl_up_sync(0xffffffffu, oa, o);
-          const float nb = __shfl_up_sync(0xffffffffu, ob, o);
-          const float na2 = __shfl_up_sync(0xffffffffu, oa2, o);
-          const float nb2 = __shfl_up_sync(0xffffffffu, ob2, o);
-          if (lane >= o) {
-            oa += na;
-            ob += nb;
-            oa2 += na2;
-            ob2 += nb2;
+          up(ia, o);
+          up(ib, o);
+          if (two) {
+            up(ia2, o);
+            up(ib2, o);
           }
         }
         if (lane == 31) {
-          gtot[g][wq][0] = oa;
-          gtot[g][wq][1] = ob;
-          gtot[g][wq][2] = oa2;
-          gtot[g][wq][3] = ob2;
+          gtot[g][wq][0] = ia.hi;
+          gtot[g][wq][1] = ia.lo;
+          gtot[g][wq][2] = ib.hi;
+          gtot[g][wq][3] = ib.lo;
+          gtot[g][wq][4] = ia2.hi;
+          gtot[g][wq][5] = ia2.lo;
+          gtot[g][wq][6] = ib2.hi;
+          gtot[g][wq][7] = ib2.lo;
         }
-        oa -= ra;
-        ob -= rb;
-        oa2 -= ra2;
-        ob2 -= rb2;
         group_bar(g);
-        float totB = 0.f, totB2 = 0.f;
+        // 3. this lane's offset (everything before its first position) and
+        //    the group's total of z (and y)
+        auto neg = [](const TwoSum& v) {
+          TwoSum n;
+          n.hi = -v.hi;
+          n.lo = -v.lo;
+          return n;
+        };
+        TwoSum oa = ia, ob = ib, oa2 = ia2, ob2 = ib2;
+        oa.add(neg(la));
+        ob.add(neg(lb));
+        oa2.add(neg(la2));
+        ob2.add(neg(lb2));
+        TwoSum totB, totB2;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+          TwoSum ea, eb, ea2, eb2;
+          ea.hi = gtot[g][q][0];
+          ea.lo = gtot[g][q][1];
+          eb.hi = gtot[g][q][2];
+          eb.lo = gtot[g][q][3];
+          ea2.hi = gtot[g][q][4];
+          ea2.lo = gtot[g][q][5];
+          eb2.hi = gtot[g][q][6];
+          eb2.lo = gtot[g][q][7];
           if (q < wq) {
-            oa += gtot[g][q][0];
-            ob += gtot[g][q][1];
-            oa2 += gtot[g][q][2];
-            ob2 += gtot[g][q][3];
+            oa.add(ea);
+            ob.add(eb);
+            if (two) {
+              oa2.add(ea2);
+              ob2.add(eb2);
+            }
           }
-          totB += gtot[g][q][1];
-          totB2 += gtot[g][q][3];
+          totB.add(eb);
+          if (two) totB2.add(eb2);
         }
+        // 4. walk the lane's positions again from its offset: the prefix
+        //    A_p and the suffix S_p = totB - B_p, each rounded once
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int p = p0 + k;
-          sA[dpad(p)] += oa;
-          sB[dpad(p)] += ob;
-          if (two) {
-            sA2[dpad(p)] += oa2;
-            sB2[dpad(p)] += ob2;
+          if (p < D) {
+            const int i = perm_s[dpad(p)];
+            const float y = yfull[i];
+            const float c = cs_s[dpad(p)];
+            const float z = sgnf(wm_s[i]) * y;
+            oa.add_prod(c, z);
+            ob.add(z);
+            TwoSum sb = totB;
+            sb.add(neg(ob));
+            sA[dpad(p)] = oa.value();
+            sS[dpad(p)] = sb.value();
+            if (two) {
+              oa2.add_prod(c, y);
+              ob2.add(y);
+              TwoSum sb2 = totB2;
+              sb2.add(neg(ob2));
+              sA2[dpad(p)] = oa2.value();
+              sS2[dpad(p)] = sb2.value();
+            }
           }
         }
         group_bar(g);
         for (int i = tg; i < D; i += 128) {
           const float wi = wm_s[i], ci = fabsf(wi);
           const int q = dpad(ub_s[i]);
-          float v = sgnf(wi) * (sA[q] + ci * (totB - sB[q]));
-          if (two) v = 0.5f * (v + (sA2[q] + ci * (totB2 - sB2[q])));
+          float v = sgnf(wi) * fmaf(ci, sS[q], sA[q]);
+          if (two) v = 0.5f * (v + fmaf(ci, sS2[q], sA2[q]));
           cb[i] += v;
         }
       }
@@ -529,16 +599,19 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
         v[q] = q < nq ? cq[d] : 0.f;
         v[CS + q] = second ? cq[a.D_pad + d] : 0.f;
       }
-      // components in order m = 0, 1, ..., 2 CS - 1
-      float sub = 0.f;
+      // u = y - sum_m P_m y, compensated, rounded once (the groups' sums in
+      // the order of their first components m = 0, 1, ..., 2 CS - 1)
+      TwoSum uc;
+      uc.add(ys[i]);
 #pragma unroll
-      for (int q = 0; q < 2 * CS; ++q) sub += v[q];
-      u[i] = d < D ? ys[i] - sub : 0.f;
+      for (int q = 0; q < 2 * CS; ++q) uc.add(-v[q]);
+      u[i] = d < D ? uc.value() : 0.f;
     }
   } else {
     for (int i = threadIdx.x; i < RS; i += NT) u[i] = ys[i];
   }
   __syncthreads();
+  if (stamp) t_defl = gtimer_u64();
   // 3. norm over the cluster
   Kahan k;
   for (int i = threadIdx.x; i < RS; i += NT) {
@@ -585,6 +658,25 @@ __device__ void pair_epilogue(const PairArgs& a, cg::cluster_group& cluster, flo
     a.ctl->counter = 0;
     __threadfence();
   }
+  if (stamp) {
+    volatile PairPhases* ph = a.phases;
+    const unsigned long long t_end = gtimer_u64();
+    const unsigned long long t0 = ph->start_min;
+    const unsigned long long lmin = ph->loop_min, lmax = ph->loop_max;
+    if (ph->prev_end && t0 > ph->prev_end) ph->sum[0] += t0 - ph->prev_end;
+    ph->sum[1] += lmin - t0;
+    ph->sum[2] += lmax - t0;
+    ph->sum[3] += t_elect - lmax;
+    ph->sum[4] += t_reduce - t_elect;
+    ph->sum[5] += t_defl - t_reduce;
+    ph->sum[6] += t_end - t_defl;
+    ph->sum[7] += 1;
+    ph->prev_end = t_end;
+    ph->start_min = ~0ull;
+    ph->loop_min = ~0ull;
+    ph->loop_max = 0;
+    __threadfence();
+  }
   cluster.sync();  // peers may still read this CTA's shared memory until here
 }
 
@@ -613,6 +705,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
   __shared__ float4 wp[RC];                 // (lo, hi, s, 0) per row of this CTA
   __shared__ float tbuf[2][kPairWarps][TC];  // per-warp column partials (by tile parity)
   __shared__ float tin[4][kPairCluster][TC];  // column partials pushed by each CTA
+  __shared__ __align__(8) uint64_t never;  // nothing ever arrives here
   __shared__ int s_err;
   __shared__ int s_last;
 
@@ -622,9 +715,17 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
     s_last = 0;
     for (int s = 0; s < kPairStages; ++s) mbar_init(&full[s], 1);
     for (int q = 0; q < 4; ++q) mbar_init(&tready[q], 1);
+    mbar_init(&never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // Fault-detection test (stall_ns > 0, never in a normal solve): thread 0
+  // waits on a barrier that nothing arrives at, through the same bounded
+  // wait as every tile and exchange.  No copy or peer store is pending on
+  // it, so the wait simply runs out; the step then computes as usual and
+  // reports the expiry as MAPI_ETIMEOUT, which stops the solve.
+  bool stalled = false;
+  if (a.stall_ns > 0 && threadIdx.x == 0) stalled = !mbar_wait(&never, 0, a.stall_ns);
   // the tiles read last stay in L2 for the next step (which walks the other
   // way); the others leave L2 first
   const uint64_t pol_first = createpolicy_evict_first();
@@ -652,6 +753,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
     __syncthreads();
     return;
   }
+  if (a.phases && threadIdx.x == 0) atomicMin(&a.phases->start_min, gtimer_u64());
   for (int r = threadIdx.x; r < RC; r += blockDim.x) {
     const int d = (int)crank * RC + r;
     const float wv = d < a.D ? a.w[d] : 0.f;
@@ -775,10 +877,15 @@ __global__ void __launch_bounds__(kPairWarps * 32, 2)
     if ((lane & (grp - 1)) == 0)
       a.ypart[(int64_t)cid * a.D_pad + rbase + lane / grp] = acc[0];
   }
-  if (threadIdx.x == 0 && s_err) {
+  if (threadIdx.x == 0 && (s_err || stalled)) {
     // a tile or a peer's partials never arrived: report it; the solve stops
     a.ctl->v[0].status = MAPI_ETIMEOUT;
     a.ctl->v[0].done = 1;
+  }
+  if (a.phases && threadIdx.x == 0) {
+    const unsigned long long t = gtimer_u64();
+    atomicMin(&a.phases->loop_min, t);
+    atomicMax(&a.phases->loop_max, t);
   }
   // the next step's kernel may launch now (it waits for this grid to finish
   // before it reads anything this step writes)
@@ -985,6 +1092,8 @@ static mapi_status launch_pair_step(mapi_ctx* ctx, cudaStream_t s, const PairLau
   pa.defl = defl;
   pa.norm_l2 = norm_l2;
   pa.denom = denom;
+  pa.stall_ns = ctx->stall_ns;
+  pa.phases = ctx->phases_on ? (PairPhases*)ctx->pair_phases.p : nullptr;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1191,7 +1300,9 @@ mapi_status run_pca(mapi_ctx* ctx, const mapi_mat* X, int k, int mode, mapi_op o
                               (int64_t)(uintptr_t)ctx->wbuf0.p,
                               (int64_t)(uintptr_t)ctx->ypart.p,
                               (int64_t)(uintptr_t)ctx->pca_c0.p,
-                              (int64_t)(uintptr_t)ctx->pca_defl.p};
+                              (int64_t)(uintptr_t)ctx->pca_defl.p,
+                              (int64_t)ctx->stall_ns,
+                              (int64_t)(ctx->phases_on ? (uintptr_t)ctx->pair_phases.p : 0)};
   GraphEntry* ge = nullptr;
   st = launch_cached_graph(
       ctx, key, [&](cudaStream_t cs) { return pca_enqueue(ctx, cs, X, p, w0, P_out); }, &ge);

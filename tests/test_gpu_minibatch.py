@@ -4,10 +4,10 @@ oracle on the same sample draws: MIN1, MIN2 and the momentum power method
 groups, batches that fill several staging chunks, the full-size synthetic set
 of the §3.2 comparison, and the error cases.
 
-Tolerance: each entry of A_t is a sum of s FP32 terms (relative error at
-most about s u, u = 2^-24, so 6e-5 at s = 1000, far less in practice); the
-iteration carries it through T normalised steps without growing it, so the
-l1 distance of the unit-l2 results stays below 2e-4 for every case here."""
+Tolerance: the FP32 bar, relative l1 1e-5.  Each entry of A_t is a sum of
+s FP32 terms split over thread groups (bound about s u, u = 2^-24, in the
+worst case; random-walk growth in practice), and the normalised steps do not
+grow it: the largest distance measured over these cases is 2.1e-6."""
 import numpy as np
 import pytest
 import torch
@@ -19,7 +19,7 @@ from tests.helpers import rel_l1, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
-TOL = 2e-4
+TOL = 1e-5
 
 
 def run(ctx, X, batch, beta, op, w0, final_l2=True):

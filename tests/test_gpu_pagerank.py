@@ -68,3 +68,25 @@ def test_pagerank_int16_bit_exact(mapi_ctx):
         np.testing.assert_array_equal(np.rint(to_host(w) * 2.0 ** q).astype(np.int64), want)
     finally:
         M.mapi_matrix_free(mapi_ctx, G)
+
+
+def test_pagerank_int16_bit_exact_full_size(mapi_ctx):
+    """The dense PageRank workload, n = 16384 (Barabasi-Albert m = 8, seed 0):
+    the int16 copy iterated in exact integers (INT32 products, INT64 norm,
+    the n integer divisions) equals the oracle's integer MAPI bit for bit."""
+    n, T = 16384, 4
+    ip, ix, dip, dix = graph(n, 8, 0)
+    w0 = datagen.start_vector(n, seed=0, low=0.0, high=1.0)
+    G32 = oracle.google_matrix(n, ip, ix, 0.85).astype(np.float32)
+    q = oracle.int_scale(G32, 16)
+    Gq = oracle.quant_int(G32, q)
+    del G32
+    G = M.mapi_google_matrix(mapi_ctx, dip, dix, n, 0.85, "i16")
+    try:
+        assert M.mapi_matrix_info(G)["int_scale_log2"] == q
+        w, it, _ = M.mapi_iterate(mapi_ctx, G, "min1", to_dev(w0), T)
+        st, want, oit, _ = oracle.mapi_int("min1", Gq, q, w0, T)
+        assert st == oracle.OK and it[0] == oit == T
+        np.testing.assert_array_equal(np.rint(to_host(w) * 2.0 ** q).astype(np.int64), want)
+    finally:
+        M.mapi_matrix_free(mapi_ctx, G)
