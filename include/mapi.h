@@ -358,8 +358,9 @@ mapi_status mapi_pagerank_sparse(mapi_ctx* ctx, const int* indptr, const int* in
 /* Kernel classes timed by mapi_profile. */
 typedef enum {
   MAPI_KC_GEMV = 0,        /* K1 MAVP-GEMV step (Alg. 1 steps 3-4) */
-  MAPI_KC_PAIR = 1,        /* pair step over X, its reduction, deflation and
-                              normalisation included (one kernel) */
+  MAPI_KC_PAIR = 1,        /* pair steps over X, their reduction, deflation and
+                              normalisation included: one persistent launch
+                              per component, counted as max_iters steps */
   MAPI_KC_PAIR_FINISH = 2, /* reserved: the pair step has no separate finish
                               kernel, so this class stays empty */
   MAPI_KC_MINCOV = 3,      /* min-covariance build, Eq. (5) */
@@ -389,13 +390,13 @@ mapi_status mapi_get_stats(mapi_ctx* ctx, mapi_stats* out, int reset);
 /* Phase time stamps of the pair step (the PCA pair mode of mapi_pca_topk).
  * Synchronises ctx's stream, then writes to out_us (8 doubles, may be NULL)
  * what was stamped since stamping was last switched on: [0] the steps
- * stamped, then per step, in microseconds of %globaltimer: [1] from the end
- * of the previous step's epilogue to the earliest start of this step's CTAs
- * (after the programmatic-dependency wait), [2] from that start to the first
- * CTA's end of its tile loop, [3] to the last CTA's, [4] from the last loop
- * end to the election of the epilogue cluster, [5] the reduction of the
- * cluster partials, [6] the deflation, [7] norm, normalisation and stop
- * test.  enable != 0 then clears the stamps and stamps later pair steps;
+ * stamped, then per step, in microseconds of %globaltimer: [1] from the
+ * publication of the previous step's iterate to the earliest start of this
+ * step's streaming CTAs, [2] from that start to the first streaming CTA's
+ * end of its tiles, [3] to the last one's, [4] from that last arrival until
+ * the epilogue cluster sees it, [5] the reduction of the accumulated row
+ * sums, [6] the deflation, [7] norm, normalisation, stop test and
+ * publication.  enable != 0 then clears the stamps and stamps later pair steps;
  * enable == 0 stops.  A few global atomics per CTA and step while on.
  * Not part of the method: it shows where a step's time goes. */
 mapi_status mapi_pair_phases(mapi_ctx* ctx, int enable, double* out_us);

@@ -432,8 +432,8 @@ def mapi_profile(ctx, enable: bool = True) -> None:
     _check(load().mapi_profile(ctx, 1 if enable else 0), "mapi_profile", ctx)
 
 
-PAIR_PHASES = ("steps", "gap_to_start", "start_to_first_loop_end", "start_to_last_loop_end",
-               "last_loop_end_to_elected", "reduce_partials", "deflate", "norm_and_stop")
+PAIR_PHASES = ("steps", "publish_to_start", "start_to_first_arrival", "start_to_last_arrival",
+               "last_arrival_to_epilogue", "reduce_rows", "deflate", "norm_stop_publish")
 
 
 def mapi_pair_phases(ctx, enable: bool = True) -> dict:

@@ -64,7 +64,7 @@ cudaEvent_t prof_begin(mapi_ctx* ctx, cudaStream_t s) {
 }
 
 void prof_end(mapi_ctx* ctx, cudaStream_t s, cudaEvent_t a, int cls, double bytes,
-              double terms) {
+              double terms, int count) {
   if (!a) return;
   cudaEvent_t b = prof_begin(ctx, s);
   if (!b) {
@@ -72,7 +72,7 @@ void prof_end(mapi_ctx* ctx, cudaStream_t s, cudaEvent_t a, int cls, double byte
     return;
   }
   std::vector<ProfMark>* sink = ctx->mark_sink ? ctx->mark_sink : &ctx->pending;
-  sink->push_back(ProfMark{cls, a, b, bytes, terms});
+  sink->push_back(ProfMark{cls, a, b, bytes, terms, count});
 }
 
 void prof_collect(mapi_ctx* ctx, std::vector<ProfMark>& marks, bool recycle) {
@@ -80,7 +80,7 @@ void prof_collect(mapi_ctx* ctx, std::vector<ProfMark>& marks, bool recycle) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess && m.cls >= 0 &&
         m.cls < MAPI_KC_COUNT) {
-      ctx->stats.timed[m.cls] += 1;
+      ctx->stats.timed[m.cls] += (uint64_t)m.count;
       ctx->stats.ms[m.cls] += ms;
       ctx->stats.bytes[m.cls] += m.bytes;
       ctx->stats.terms[m.cls] += m.terms;

@@ -1,6 +1,7 @@
 // Internal declarations of the MAPI CUDA library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -87,6 +88,7 @@ struct ProfMark {
   int cls;
   cudaEvent_t a, b;
   double bytes, terms;
+  int count;  // launches (or persistent-kernel steps) the two events bracket
 };
 
 struct GraphEntry {
@@ -102,13 +104,14 @@ struct Server;
 
 namespace mapi {
 // Time stamps of pair steps (%globaltimer, ns), filled while phase stamping
-// is on: the earliest start of the current step's CTAs (after the
-// dependency wait), the earliest and latest end of a CTA's tile loop, the
-// end of the previous step, and per phase the nanoseconds summed over the
-// steps: [0] previous end -> start, [1] start -> first loop end, [2] start
-// -> last loop end, [3] last loop end -> epilogue elected, [4] reduction of
-// the cluster partials, [5] deflation, [6] norm, normalisation and stop
-// test, [7] steps stamped.
+// is on: the earliest start of the current step's streaming CTAs (after the
+// published iterate arrived), the first and last arrival of a streaming CTA
+// at the end of its tiles, the previous step's publication, and per phase
+// the nanoseconds summed over the steps: [0] previous publication -> start,
+// [1] start -> first arrival, [2] start -> last arrival, [3] last arrival ->
+// the epilogue cluster sees it, [4] reduction of the accumulated row sums,
+// [5] deflation and its combination over the cluster, [6] norm,
+// normalisation, stop test and publication, [7] steps stamped.
 struct PairPhases {
   unsigned long long start_min, loop_min, loop_max, prev_end;
   unsigned long long sum[8];
@@ -150,6 +153,7 @@ struct mapi_ctx {
   bool phases_on = false;      // stamp the phases of pair steps
   DevBuf pair_phases;          // one mapi::PairPhases
   long long stall_ns = 0;      // > 0: fault-detection test of the bounded waits
+  int pair_coop = -1;          // cooperative cluster launch accepted (-1: not asked)
   // K1 may run in 8-CTA clusters on large matrices; off for
   // the serving loop, whose solves share the GPU with a persistent batched
   // launch (a cluster waits for eight free CTA slots at once)
@@ -187,7 +191,7 @@ inline void count_launch(mapi_ctx* ctx, uint64_t n = 1) {
 cudaEvent_t prof_begin(mapi_ctx* ctx, cudaStream_t s);
 // End it: records the stop event and files the mark.
 void prof_end(mapi_ctx* ctx, cudaStream_t s, cudaEvent_t a, int cls, double bytes,
-              double terms);
+              double terms, int count = 1);
 // Fold completed marks into the counters (stream already synchronised).
 void prof_collect(mapi_ctx* ctx, std::vector<ProfMark>& marks, bool recycle);
 void destroy_graph(mapi_ctx* ctx, GraphEntry& g);
@@ -286,6 +290,42 @@ mapi_status launch_outer_apply(mapi_ctx* ctx, mapi_op op, int D, int nprev, Oute
 mapi_status launch_deflate_mincov(mapi_ctx* ctx, mapi_op op, const float* P, int64_t ldp, int c,
                                   int D, const float* C, int64_t ld, float* T, void* rank,
                                   int kslots, int64_t stride, float* Cc, cudaStream_t s);
+
+// Pair-mode PCA (pair.cu): every step of one component in one persistent
+// launch.  The earlier components the iterate is deflated by, ranked by
+// launch_outer_prep: perm[p] = index at sorted position p, wsort[p] = wt at
+// that position, ubi[i] = the last sorted position whose |wt| is <= |wt_i|.
+struct DeflArgs {
+  int nprev;          // finished components to deflate (0: none)
+  int op;             // MAPI_OP_MIN1 / MIN2 / DOT
+  const float* P;     // outer-product vectors wt, column m at P + m * ldp
+  int64_t ldp;
+  const int* perm;    // [m][stride] per component
+  const float* wsort;
+  const int* ubi;
+  int64_t stride;     // elements between components in perm / wsort / ubi
+};
+struct PairPlan {
+  const void* fn = nullptr;
+  int rw = 0;          // rows per warp (8, 16, 32)
+  int clusters = 0;    // 4-CTA clusters of the launch, the epilogue's included
+  int D_pad = 0;       // rows one cluster covers (4 x 8 x rw)
+  size_t smem = 0;     // dynamic shared memory per CTA
+  bool coop = false;   // cooperative launch accepted
+  CUtensorMap map;     // X as [rows_pad][ld], one (columns x rows) box per tile
+};
+mapi_status plan_pair(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, PairPlan* pl);
+// Device scratch of a pair solve: the fixed-point accumulators and the
+// launch's shared state.
+size_t pair_scratch_bytes(const PairPlan& pl);
+// Once per solve: clear the scratch and find max |X|.
+mapi_status launch_pair_prepare(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
+                                const mapi_mat* X, void* scratch);
+// T steps of one component (start vector already in wb0, control block set).
+mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
+                              const mapi_mat* X, void* scratch, float* wb0, float* wb1,
+                              const DeflArgs& defl, IterCtl* ctl, int T, int norm_l2,
+                              float denom, int dir0);
 
 // Batched solves (batched.cu): one instance as the kernel sees it.
 struct BatchDev {
