@@ -112,7 +112,7 @@ __device__ unsigned wait_geq(const unsigned* p, unsigned target) {
     if (v >= target) return v;
     if (i == 0) t0 = globaltimer_ns();
     else if (globaltimer_ns() - t0 > kWaitLimitNs) return 0;
-    if (i > 64) __nanosleep(64);
+    if (i > 4096) __nanosleep(32);
   }
 }
 
@@ -142,6 +142,25 @@ __device__ __forceinline__ float cluster_sum(cg::cluster_group& cluster, float* 
   }
   __syncthreads();
   const float r = *bcast;
+  __syncthreads();
+  return r;
+}
+
+// Two such sums at once, in one pass: slot[0] and slot[1] of every CTA,
+// each added in a fixed order; every thread of the block gets both.
+__device__ __forceinline__ float2 cluster_sum2(cg::cluster_group& cluster, float* slot,
+                                               float* bcast) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    const int which = lane >> 2, rk = lane & 3;
+    float v = which < 2 ? cluster.map_shared_rank(slot, rk)[which] : 0.f;
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    if (lane == 0) bcast[0] = v;
+    if (lane == 4) bcast[1] = v;
+  }
+  __syncthreads();
+  const float2 r = make_float2(bcast[0], bcast[1]);
   __syncthreads();
   return r;
 }
@@ -467,11 +486,12 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
     const float np = block_sum<NT>(k.value(), red);
     if (threadIdx.x == 0) {
       part[0] = np;
-      part[2] = *(volatile const int*)&a.sync->err ? 1.f : 0.f;
+      part[1] = *(volatile const int*)&a.sync->err ? 1.f : 0.f;
     }
     cluster.sync();  // also: peers have finished reading this CTA's cbuf
-    float L = cluster_sum(cluster, &part[0], &part[4]);
-    const bool err = cluster_sum(cluster, &part[2], &part[5]) > 0.f;
+    const float2 Le = cluster_sum2(cluster, &part[0], &part[4]);
+    float L = Le.x;
+    const bool err = Le.y > 0.f;
     if (a.norm_l2) L = sqrtf(L);
     const bool ok = (L > 0.f) && isfinite(L);
     // 5. normalise own rows (the n divisions of §2.2), the delta when a stop
@@ -491,9 +511,9 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
     float Dsum = 0.f;
     if (want_delta) {
       const float dp = block_sum<NT>(dk.value(), red);
-      if (threadIdx.x == 0) part[1] = dp;
+      if (threadIdx.x == 0) part[2] = dp;
       cluster.sync();
-      Dsum = cluster_sum(cluster, &part[1], &part[6]);
+      Dsum = cluster_sum(cluster, &part[2], &part[6]);
     }
     const bool done = !ok || err || (want_delta && Dsum < a.ctl->tol) || t + 1 == a.T;
     if (r == 0 && threadIdx.x == 0) {
