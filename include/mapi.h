@@ -350,6 +350,43 @@ mapi_status mapi_pagerank_sparse(mapi_ctx* ctx, const int* indptr, const int* in
 
 
 /* ------------------------------------------------------------------ */
+/* Pieces of a partitioned solve.  When the data is split over processes */
+/* (one GPU each), each rank computes the unnormalised product of its    */
+/* shard, the ranks combine them (a gather of row blocks, or a sum of    */
+/* column-shard partials), and the normalisation of Eq. (6) (and, for    */
+/* PCA, the deflation of Alg. 2 step 6) is applied to the whole vector.  */
+/* ------------------------------------------------------------------ */
+
+/*
+ * y_out[r] = a_i^T (+) w for the rows i = row_begin + r < row_end of A: the
+ * matrix-vector product of Alg. 1 step 3 (matrix extension of §2.1) for a
+ * block of rows, before the l1 normalisation.  Row-partitioned MAPI: rank k
+ * holds all of w and its rows' results; gathering the blocks gives A (+) w.
+ *   A: packed matrix in F32, BF16 or FP8 storage (integer storage has the
+ *      exact path of mapi_iterate only: MAPI_EINVAL).
+ *   op: MIN1, MIN2 or DOT.  w: device, A->cols FP32 (used as given).
+ *   y_out: device, row_end - row_begin FP32 (caller-owned).
+ * FP32 accumulation (one warp per row).  MAPI_EINVAL for rows outside A.
+ * Synchronous on the context's stream.
+ */
+mapi_status mapi_rows_product(mapi_ctx* ctx, const mapi_mat* A, int row_begin, int row_end,
+                              mapi_op op, const float* w, float* y_out);
+
+/*
+ * The pair product of the PCA pair mode on X (D x N) without its
+ * denominator, deflation or normalisation:
+ *   t_n = x_n^T (+) w,  y_out[d] = sum_n X_dn (+) t_n.
+ * Column-partitioned PCA: rank k holds the columns (samples) of its shard as
+ * its own X; the sum of the ranks' y_out is the product over all of X, since
+ * t_n depends only on column n.  w: device, D FP32, used as given.  y_out:
+ * device, D FP32.  Same kernel as the pair mode of mapi_pca_topk (one step;
+ * row sums added exactly in 64-bit fixed point).  X in F32 or BF16 storage,
+ * D <= 1024; op MIN1, MIN2 or DOT.  Synchronous.
+ */
+mapi_status mapi_pair_partial(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, const float* w,
+                              float* y_out);
+
+/* ------------------------------------------------------------------ */
 /* Diagnostics: kernel timing and launch counting.  Not part of the    */
 /* paper's method; they let a caller measure the kernels against their */
 /* rooflines without an external profiler.                             */

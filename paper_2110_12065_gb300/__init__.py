@@ -27,6 +27,7 @@ __all__ = [
     "mapi_autotune_batched", "mapi_submit", "mapi_poll", "mapi_cancel",
     "mapi_pagerank_sparse", "mapi_iterate_switch", "mapi_minibatch_momentum",
     "mapi_mavp_project", "mapi_image_reconstruct", "mapi_pair_phases", "mapi_debug_stall",
+    "mapi_rows_product", "mapi_pair_partial",
     "KERNEL_CLASSES",
     "OP", "ST", "FLAG_FINAL_L2", "FLAG_RAW_START", "SCALE_AUTO",
     "PCA_MINCOV", "PCA_PAIR", "STATUS",
@@ -121,6 +122,8 @@ def load(path: str | None = None):
         "mapi_pagerank_sparse": [p_, p_, p_, i, d, i, p_, i, d, p_, p_, p_],
         "mapi_profile": [p_, i],
         "mapi_pair_phases": [p_, i, p_],
+        "mapi_rows_product": [p_, p_, i, i, i, p_, p_],
+        "mapi_pair_partial": [p_, p_, i, p_, p_],
         "mapi_debug_stall": [p_, i64],
         "mapi_get_stats": [p_, C.POINTER(_Stats), i],
         "mapi_iterate_noalloc": [p_, i, i64, i, p_, i, d, u, p_, p_, p_, p_],
@@ -430,6 +433,32 @@ def mapi_pagerank_sparse(ctx, indptr, indices, n: int, w0, max_iters: int,
 def mapi_profile(ctx, enable: bool = True) -> None:
     """Time the library's streaming kernels with CUDA events on their stream."""
     _check(load().mapi_profile(ctx, 1 if enable else 0), "mapi_profile", ctx)
+
+
+def mapi_rows_product(ctx, A, row_begin: int, row_end: int, op, w, y_out=None):
+    """y[r] = a_(row_begin + r)^T (+) w for a block of rows of packed A
+    (unnormalised; a row shard of Alg. 1 step 3).  w: torch CUDA float32."""
+    torch = _torch()
+    if y_out is None:
+        y_out = torch.empty(max(0, row_end - row_begin), dtype=torch.float32, device=w.device)
+    opi = OP[op] if isinstance(op, str) else int(op)
+    _check(load().mapi_rows_product(ctx, A, int(row_begin), int(row_end), opi,
+                                    C.c_void_p(_dptr(w)), C.c_void_p(_dptr(y_out))),
+           "mapi_rows_product", ctx)
+    return y_out
+
+
+def mapi_pair_partial(ctx, X, op, w, y_out=None):
+    """Unnormalised pair product of packed X (D x N): y_d = sum_n X_dn (+)
+    (x_n^T (+) w), a column shard's partial.  w: torch CUDA float32 (D,)."""
+    torch = _torch()
+    if y_out is None:
+        y_out = torch.empty_like(w)
+    opi = OP[op] if isinstance(op, str) else int(op)
+    _check(load().mapi_pair_partial(ctx, X, opi, C.c_void_p(_dptr(w)),
+                                    C.c_void_p(_dptr(y_out))),
+           "mapi_pair_partial", ctx)
+    return y_out
 
 
 PAIR_PHASES = ("steps", "publish_to_start", "start_to_first_arrival", "start_to_last_arrival",

@@ -632,6 +632,30 @@ mapi_status mapi_mincov(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, double den
   return launch_mincov_raw(ctx, X, op, (float)denom, C_out, X->rows, ctx->stream);
 }
 
+mapi_status mapi_rows_product(mapi_ctx* ctx, const mapi_mat* A, int row_begin, int row_end,
+                              mapi_op op, const float* w, float* y_out) {
+  if (!ctx) return MAPI_EINVAL;
+  if (!valid_matrix(ctx, A) || !w || !y_out) return fail(ctx, MAPI_EINVAL, "bad argument");
+  if (row_begin < 0 || row_end < row_begin || row_end > A->rows)
+    return fail(ctx, MAPI_EINVAL, "rows outside the matrix");
+  DeviceGuard g(ctx->device);
+  mapi_status st = launch_rows_raw(ctx, A, row_begin, row_end - row_begin, op, w, y_out,
+                                   ctx->stream);
+  if (st != MAPI_OK) return st;
+  MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return MAPI_OK;
+}
+
+mapi_status mapi_pair_partial(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, const float* w,
+                              float* y_out) {
+  if (!ctx) return MAPI_EINVAL;
+  if (!valid_matrix(ctx, X) || !w || !y_out) return fail(ctx, MAPI_EINVAL, "bad argument");
+  if (op != MAPI_OP_MIN1 && op != MAPI_OP_MIN2 && op != MAPI_OP_DOT)
+    return fail(ctx, MAPI_EINVAL, "pair step needs MIN1, MIN2 or DOT");
+  DeviceGuard g(ctx->device);
+  return run_pair_partial(ctx, X, op, w, y_out);
+}
+
 mapi_status mapi_pca_topk(mapi_ctx* ctx, const mapi_mat* X, int k, int mode, mapi_op op,
                           int iters_per_vec, double tol_l1, double cov_denom, const float* w0,
                           float* P_out, int* iters_done) {

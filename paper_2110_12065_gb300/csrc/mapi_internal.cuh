@@ -325,7 +325,14 @@ mapi_status launch_pair_prepare(mapi_ctx* ctx, cudaStream_t s, const PairPlan& p
 mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
                               const mapi_mat* X, void* scratch, float* wb0, float* wb1,
                               const DeflArgs& defl, IterCtl* ctl, int T, int norm_l2,
-                              float denom, int dir0);
+                              float denom, int dir0, float* raw_out = nullptr);
+// y[r] = a_{row_begin + r}^T (+) w for r < rows, no normalisation (shard.cu).
+mapi_status launch_rows_raw(mapi_ctx* ctx, const mapi_mat* A, int row_begin, int rows,
+                            mapi_op op, const float* w, float* y, cudaStream_t s);
+// One unnormalised pair product of X (y_d = sum_n X_dn (+) (x_n^T (+) w),
+// no denominator, deflation or normalisation) into y (device, D floats).
+mapi_status run_pair_partial(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, const float* w,
+                             float* y);
 
 // Batched solves (batched.cu): one instance as the kernel sees it.
 struct BatchDev {

@@ -72,6 +72,7 @@ struct PairSolveArgs {
   DeflArgs defl;
   long long stall_ns;  // > 0: fault-detection test (mapi_debug_stall)
   PairPhases* phases;  // non-null: phase stamps (mapi_pair_phases)
+  float* raw_out;      // non-null: one step, its y (no deflation or norm) written here
 };
 
 template <int ST>
@@ -279,6 +280,23 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
     __syncthreads();
     for (int i = threadIdx.x; i < RS; i += NT) ys[i] = yfull[r0 + i];
     if (stamp) t_reduce = gtimer_u64();
+    if (a.raw_out) {  // one unnormalised pair product (a column shard's partial)
+      for (int i = threadIdx.x; i < RS; i += NT)
+        if (r0 + i < D) a.raw_out[r0 + i] = ys[i];
+      if (r == 0 && threadIdx.x == 0) {
+        VecState* st = &a.ctl->v[0];
+        st->iters = 1;
+        st->done = 1;
+        if (*(volatile const int*)&a.sync->err) st->status = MAPI_ETIMEOUT;
+        a.ctl->all_done = 1;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        st_release_u32(&a.sync->pub[r], 3u);
+      }
+      break;
+    }
     // 3. deflation: group g = warps 4g .. 4g + 3 takes component r + CS g
     //    (and every 2 CS-th after it); warp wq of the group scans sorted
     //    positions [256 wq, 256 wq + 256), eight per lane.  Every sum is
@@ -999,7 +1017,7 @@ static int pair_keep_tiles(const mapi_ctx* ctx, const mapi_mat* X, const PairPla
 mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
                               const mapi_mat* X, void* scratch, float* wb0, float* wb1,
                               const DeflArgs& defl, IterCtl* ctl, int T, int norm_l2,
-                              float denom, int dir0) {
+                              float denom, int dir0, float* raw_out) {
   if (T <= 0) return MAPI_OK;
   const int TCc = (X->storage == MAPI_ST_F32) ? 32 : 64;
   const int64_t ntiles = (X->ld + TCc - 1) / TCc;
@@ -1031,6 +1049,7 @@ mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
   a.defl = defl;
   a.stall_ns = ctx->stall_ns;
   a.phases = ctx->phases_on ? (PairPhases*)ctx->pair_phases.p : nullptr;
+  a.raw_out = raw_out;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;

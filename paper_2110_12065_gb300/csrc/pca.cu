@@ -342,6 +342,39 @@ mapi_status pca_enqueue(mapi_ctx* ctx, cudaStream_t s, const mapi_mat* X, const 
 
 }  // namespace
 
+mapi_status run_pair_partial(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, const float* w,
+                             float* y) {
+  PairPlan pl;
+  mapi_status st;
+  if ((st = plan_pair(ctx, X, op, &pl)) != MAPI_OK) return st;
+  const int64_t wst = (pl.D_pad + 15) / 16 * 16;
+  if ((st = ensure(ctx, ctx->wbuf0, sizeof(float) * wst)) != MAPI_OK ||
+      (st = ensure(ctx, ctx->wbuf1, sizeof(float) * wst)) != MAPI_OK ||
+      (st = ensure(ctx, ctx->ypart, pair_scratch_bytes(pl))) != MAPI_OK ||
+      (st = ensure(ctx, ctx->ctl, sizeof(IterCtl))) != MAPI_OK)
+    return st;
+  cudaStream_t s = ctx->stream;
+  float* wb0 = (float*)ctx->wbuf0.p;
+  float* wb1 = (float*)ctx->wbuf1.p;
+  IterCtl* ctl = (IterCtl*)ctx->ctl.p;
+  if ((st = launch_pair_prepare(ctx, s, pl, X, ctx->ypart.p)) != MAPI_OK) return st;
+  // w is used as given (no start normalisation)
+  if ((st = launch_start_float(ctx, s, w, X->rows, X->rows, 1, wb0, wb1, wst, 1, ctl, 0.f)) !=
+      MAPI_OK)
+    return st;
+  DeflArgs defl{};
+  defl.op = op;
+  if ((st = launch_pair_solve(ctx, s, pl, X, ctx->ypart.p, wb0, wb1, defl, ctl, 1,
+                              op == MAPI_OP_DOT ? 1 : 0, 1.f, 0, y)) != MAPI_OK)
+    return st;
+  IterCtl h;
+  MAPI_CUDA_TRY(ctx, cudaMemcpyAsync(&h, ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, s));
+  MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (h.v[0].status != MAPI_OK)
+    return fail(ctx, (mapi_status)h.v[0].status, "pair partial did not complete");
+  return MAPI_OK;
+}
+
 mapi_status run_pca(mapi_ctx* ctx, const mapi_mat* X, int k, int mode, mapi_op op, int iters,
                     double tol, double denom, const float* w0, float* P_out, int* iters_done) {
   if (mode != MAPI_PCA_MINCOV && mode != MAPI_PCA_PAIR)
