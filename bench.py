@@ -300,11 +300,16 @@ def pair_phases(M, ctx, Xd, W0d, P, storage="f32"):
     return {k: round(v, 3) for k, v in ph.items()}
 
 
-def alu_peak_terms(sm_mhz: float = 2070.0, sms: int = 152) -> float:
-    """ALU roofline of the float MAVP term: each term needs two min/max
-    instructions on the ALU pipe, which issues 64 lanes per clock per SM
-    (16 per SM sub-partition, measured), so 32 terms per clock per SM."""
-    return 32.0 * sms * sm_mhz * 1e6
+def alu_probe(M, ctx) -> dict:
+    """Per-SM, per-clock issue rates of the MAVP term's instruction mixes,
+    measured by the library's probe kernel (SM cycles inside the kernel)."""
+    return {m: round(M.mapi_alu_probe(ctx, m), 2) for m in M.ALU_MIXES}
+
+
+def alu_peak_terms(terms_per_clk_sm: float, sm_mhz: float = 2070.0, sms: int = 152) -> float:
+    """ALU roofline of the float MAVP term: the measured FP32 min1 terms per
+    clock per SM (alu_probe) x SMs x the maximum SM clock."""
+    return terms_per_clk_sm * sms * sm_mhz * 1e6
 
 
 def timed(torch, fn, reps):
@@ -349,6 +354,8 @@ def run_variants(M, ctx, torch, dev, X, W0d, peaks):
             M.mapi_matrix_free(ctx, mat)
         return ms, st
 
+    probe = alu_probe(M, ctx)
+    out["alu_probe_per_clk_per_sm"] = probe
     out["pca_pair_f32_phases_us"] = pair_phases(M, ctx, Xd, W0d, P)
     ms, st = pca("bf16", "pair")
     pr = st["pair"]
@@ -363,11 +370,15 @@ def run_variants(M, ctx, torch, dev, X, W0d, peaks):
             "ms_per_solve": round(ms, 3), "iters_per_s": round(K_COMP * ITERS / (ms / 1e3), 1),
             "build_ms": round(mc["ms"] / max(1, mc["launches"]), 3),
             "build_terms_per_s": round(mc["terms"] / (mc["ms"] / 1e3), 1) if mc["ms"] else None,
+            "build_alu_frac": round(mc["terms"] / (mc["ms"] / 1e3) / alu_peak_terms(
+                probe["min1_term_f32"] if stg == "f32" else probe["min1_term_bf16"]), 4)
+            if mc["ms"] else None,
             "iterate_us_per_step": round(gv["ms"] / max(1, gv["launches"]) * 1e3, 3)}
 
-    # batched: Wishart instances, n log-uniform in [64, 2048], 4 start vectors,
-    # one persistent launch (1024 instances x 10 steps here)
-    sizes = datagen.wishart_sizes(1024, seed=0)
+    # batched: 4096 Wishart instances, n log-uniform in [64, 2048], 4 start
+    # vectors each, 100 steps, one persistent launch (the batched workload)
+    n_inst, steps = 4096, 100
+    sizes = datagen.wishart_sizes(n_inst, seed=0)
     for stg in ("f32", "bf16"):
         mats, items = [], []
         for k, n in enumerate(sizes):
@@ -376,15 +387,16 @@ def run_variants(M, ctx, torch, dev, X, W0d, peaks):
                                             for v in range(4)])).to(dev)
             items.append((mats[-1], w0, torch.empty_like(w0)))
         r = M.mapi_autotune_batched(ctx, items, "min1", 4, iters=2)
-        steps = 10
         run = lambda: M.mapi_iterate_batched(ctx, items, "min1", 4, steps)
-        ms = timed(torch, run, 2)
+        ms = timed(torch, run, 1)
         elems = float((sizes.astype(np.float64) ** 2).sum())
         terms = elems * 4 * steps
         eb = 4 if stg == "f32" else 2
-        peak_terms = alu_peak_terms()
-        out[f"batched_1024x4_{stg}"] = {
-            "instance_steps_per_s": round(1024 * steps / (ms / 1e3), 1),
+        peak_terms = alu_peak_terms(probe["min1_term_f32"] if stg == "f32"
+                                    else probe["min1_term_bf16"])
+        out[f"batched_{n_inst}x4_{stg}"] = {
+            "instances": n_inst, "steps": steps,
+            "instance_steps_per_s": round(n_inst * steps / (ms / 1e3), 1),
             "ms_per_launch": round(ms, 3), "rows_per_warp": r,
             "terms_per_s": round(terms / (ms / 1e3), 1),
             "alu_frac": round(terms / (ms / 1e3) / peak_terms, 4),
@@ -828,6 +840,8 @@ def run_case(case: str):
         _, _, its = M.mapi_image_reconstruct(ctx, torch.from_numpy(imgs.reshape(Nn, -1)).cuda(),
                                              k, "min2", 6, W0)
         out = f"{case}: {Nn} images of {side}x{side}, {k} components, iters {its}"
+    elif case == "alu-peak":
+        out = json.dumps({"case": case, "per_clk_per_sm": alu_probe(M, ctx)})
     elif case == "minibatch":
         X = datagen.stochastic_pca_data(10 ** 6, 10, seed=0)
         b = datagen.minibatches(10 ** 6, 100, 1000, seed=1)
@@ -870,7 +884,7 @@ def main():
                          "pair-f32, pair-bf16, pair-phases, pair-phases-bf16, "
                          "mincov-f32, mincov-bf16, pagerank-f32, "
                          "pagerank-bf16, pagerank-fp8, pagerank-i16, pagerank-sparse, batched-f32, serve, "
-                         "image, minibatch")
+                         "image, minibatch, alu-peak")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)

@@ -438,6 +438,17 @@ mapi_status mapi_get_stats(mapi_ctx* ctx, mapi_stats* out, int reset);
  * Not part of the method: it shows where a step's time goes. */
 mapi_status mapi_pair_phases(mapi_ctx* ctx, int enable, double* out_us);
 
+/* Issue-rate probe of the MAVP term (the ALU roofline of the batched and
+ * min-covariance kernels).  One full wave of blocks runs a register-resident
+ * loop of independent chains; the slowest block's SM cycles (clock64) give
+ * what one SM completes per clock, written to *per_clock_per_sm:
+ *   mix 0: FP32 min1 terms, sign(w) clamp(a, -|w|, |w|) accumulated by a
+ *          fused multiply-add by +-1 (2 min/max + 1 FMA);
+ *   mix 1: FMA instructions;  mix 2: min/max instructions;
+ *   mix 3: min1 terms on a BF16 operand widened to FP32 (1 shift + the term).
+ * Per thread-lane counts; clock-independent.  Synchronous. */
+mapi_status mapi_alu_probe(mapi_ctx* ctx, int mix, double* per_clock_per_sm);
+
 /* Failure-detection test hook.  limit_ns > 0: in every later pair step each
  * CTA also waits, through the same bounded wait as its tile copies and
  * cluster exchanges, on a barrier that nothing ever arrives at, with this

@@ -27,7 +27,7 @@ __all__ = [
     "mapi_autotune_batched", "mapi_submit", "mapi_poll", "mapi_cancel",
     "mapi_pagerank_sparse", "mapi_iterate_switch", "mapi_minibatch_momentum",
     "mapi_mavp_project", "mapi_image_reconstruct", "mapi_pair_phases", "mapi_debug_stall",
-    "mapi_rows_product", "mapi_pair_partial",
+    "mapi_rows_product", "mapi_pair_partial", "mapi_alu_probe",
     "KERNEL_CLASSES",
     "OP", "ST", "FLAG_FINAL_L2", "FLAG_RAW_START", "SCALE_AUTO",
     "PCA_MINCOV", "PCA_PAIR", "STATUS",
@@ -123,6 +123,7 @@ def load(path: str | None = None):
         "mapi_profile": [p_, i],
         "mapi_pair_phases": [p_, i, p_],
         "mapi_rows_product": [p_, p_, i, i, i, p_, p_],
+        "mapi_alu_probe": [p_, i, p_],
         "mapi_pair_partial": [p_, p_, i, p_, p_],
         "mapi_debug_stall": [p_, i64],
         "mapi_get_stats": [p_, C.POINTER(_Stats), i],
@@ -471,6 +472,17 @@ def mapi_pair_phases(ctx, enable: bool = True) -> dict:
     out = (C.c_double * 8)()
     _check(load().mapi_pair_phases(ctx, 1 if enable else 0, out), "mapi_pair_phases", ctx)
     return {k: float(v) for k, v in zip(PAIR_PHASES, out)}
+
+
+ALU_MIXES = ("min1_term_f32", "ffma", "fmnmx", "min1_term_bf16")
+
+
+def mapi_alu_probe(ctx, mix) -> float:
+    """Per-SM, per-clock rate of one instruction mix (see ALU_MIXES)."""
+    m = ALU_MIXES.index(mix) if isinstance(mix, str) else int(mix)
+    out = C.c_double()
+    _check(load().mapi_alu_probe(ctx, m, C.byref(out)), "mapi_alu_probe", ctx)
+    return out.value
 
 
 def mapi_debug_stall(ctx, limit_ns: int) -> None:
