@@ -3,9 +3,10 @@
 // thread per context owns a private child context (its own stream and
 // scratch).  Every admitted request gets its matrix built on the device (C
 // by Eq. (5), or G by Eq. (11)) and its iterate kept resident; each round
-// advances every resident solve by up to kRoundSteps steps of Alg. 1 in one
-// persistent batched launch per (storage, op), then deflates finished PCA
-// components (Alg. 2 step 6) or copies finished results to the caller.
+// advances every resident solve by up to kRoundSteps steps of Alg. 1 (to the
+// end of its current component when no request is waiting for admission)
+// in one persistent batched launch per (storage, op), then deflates finished
+// PCA components (Alg. 2 step 6) or copies finished results to the caller.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -352,9 +353,17 @@ void run_round(Server* sv) {
     if (q->n >= kWideN) wide.push_back(q);
     else groups[{(int)q->st, (int)q->r.op}].push_back(q);
   }
-  auto steps_of = [](const ServeReq* q) {
+  // with nobody waiting to be admitted, a round takes every solve to the end
+  // of its current component (fewer host round trips per request); otherwise
+  // rounds stay short so that arrivals are admitted soon
+  bool waiting;
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    waiting = !sv->queue.empty() || !sv->built.empty() || !sv->to_build.empty();
+  }
+  auto steps_of = [waiting](const ServeReq* q) {
     const int rem = q->r.max_iters - q->it_comp;
-    return rem < kRoundSteps ? rem : kRoundSteps;
+    return (!waiting || rem < kRoundSteps) ? rem : kRoundSteps;
   };
   // deflations and copies that ended the previous round ran on the loop's
   // stream: the batched launches of this round come after them
