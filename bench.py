@@ -903,10 +903,86 @@ def cpu_baseline(X, W0, seconds: float = 10.0):
     for _ in range(reps):
         one()
     dt = time.perf_counter() - t0
-    return {"value": round(reps / dt, 4), "unit": UNIT, "cores": oracle.max_threads(),
+    cores = oracle.max_threads()
+    # the same step on one host thread (a shorter sample)
+    oracle.set_num_threads(1)
+    try:
+        t1 = time.perf_counter()
+        one()
+        first1 = time.perf_counter() - t1
+        reps1 = max(1, int(0.25 * seconds / max(first1, 1e-3)))
+        t1 = time.perf_counter()
+        for _ in range(reps1):
+            one()
+        dt1 = time.perf_counter() - t1
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": round(reps / dt, 4), "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": f"{reps} pair steps (component 2, one deflation) on the full "
-                      f"D=1024 x N=65536 X, FP64, {dt:.1f} s"}
+                      f"D=1024 x N=65536 X, FP64, {dt:.1f} s",
+            "value_1_thread": round(reps1 / dt1, 4),
+            "sample_1_thread": f"{reps1} pair steps on 1 thread, {dt1:.1f} s"}
+
+
+def oracle_times():
+    """The FP64 oracle on bounded samples of each workload, on one host thread
+    and on all of them (seconds per unit stated in each entry)."""
+    import datagen
+    import oracle
+    cores = oracle.max_threads()
+
+    def timed_both(fn, reps=1):
+        out = {}
+        for name, th in (("1_thread", 1), (f"{cores}_threads", cores)):
+            oracle.set_num_threads(th)
+            fn()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            out[name] = (time.perf_counter() - t0) / reps
+        oracle.set_num_threads(cores)
+        return out
+
+    res = {"cores": cores}
+    A = datagen.symmetric_gaussian(512, seed=0)
+    w0 = datagen.start_vector(512, seed=0).astype(np.float64)
+    t = timed_both(lambda: oracle.mapi("min1", A, w0, 200), reps=3)
+    res["plain_n512_min1_s_per_iter"] = {k: v / 200 for k, v in t.items()}
+    X = datagen.spiked_pca_data(1024, 65536, seed=0).astype(np.float64)
+    w = datagen.start_vector(1024, seed=1).astype(np.float64)
+    w /= np.linalg.norm(w)
+    res["pca_pair_s_per_step"] = timed_both(lambda: oracle.pair_step("min1", X, w, 65536.0))
+    Xs = np.ascontiguousarray(X[:, :2048])
+    t = timed_both(lambda: oracle.mincov("min1", Xs, 2048.0))
+    res["pca_mincov_build_s_full_size"] = {k: v * 32 for k, v in t.items()}
+    del X, Xs
+    n = 16384
+    ip, ix = datagen.barabasi_albert_digraph(n, m=8, seed=0)
+    G = oracle.google_matrix(n, ip, ix, 0.85)
+    p0 = datagen.start_vector(n, seed=0, low=0.0, high=1.0).astype(np.float64)
+    res["pagerank_n16384_f64_s_per_step"] = timed_both(lambda: oracle.mapi("min1", G, p0, 1))
+    G32 = G.astype(np.float32)
+    del G
+    q = oracle.int_scale(G32, 16)
+    Gq = oracle.quant_int(G32, q)
+    res["pagerank_n16384_int16_s_per_step"] = timed_both(
+        lambda: oracle.mapi_int("min1", Gq, q, p0.astype(np.float32), 1))
+    del Gq, G32
+    sizes = datagen.wishart_sizes(4096, seed=0)
+    sub = [int(x) for x in sizes[:64]]
+    mats = [datagen.wishart_instance(nn, k, dtype=np.float64) for k, nn in enumerate(sub)]
+    vecs = [datagen.start_vector(nn, seed=k) for k, nn in enumerate(sub)]
+
+    def batch_step():
+        for Am, v in zip(mats, vecs):
+            for _ in range(4):
+                oracle.matvec("min1", Am, v)
+    t = timed_both(batch_step)
+    frac = float((sizes[:64].astype(np.float64) ** 2).sum() / (sizes.astype(np.float64) ** 2).sum())
+    res["batched_4096x4_s_per_step_scaled"] = {k: v / frac for k, v in t.items()}
+    res["batched_sample"] = "64 of the 4096 instances, 4 vectors, one product each, scaled by n^2"
+    return res
 
 
 def run_reference(args, rank, world):
@@ -1000,6 +1076,8 @@ def run_case(case: str):
         _, _, its = M.mapi_image_reconstruct(ctx, torch.from_numpy(imgs.reshape(Nn, -1)).cuda(),
                                              k, "min2", 6, W0)
         out = f"{case}: {Nn} images of {side}x{side}, {k} components, iters {its}"
+    elif case == "oracle-times":
+        out = json.dumps({"case": case, "oracle": oracle_times()})
     elif case == "alu-peak":
         out = json.dumps({"case": case, "per_clk_per_sm": alu_probe(M, ctx)})
     elif case == "minibatch":

@@ -104,6 +104,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 // Bounded spin until *p >= target (acquire); the value seen, or 0 when the
 // limit ran out.
 __device__ unsigned wait_geq(const unsigned* p, unsigned target) {
@@ -572,10 +575,8 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
     // 6. publish this CTA's rows (and the stop bit) to the streaming CTAs of
     //    the same rank
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
+    if (threadIdx.x == 0)
       st_release_u32(&a.sync->pub[r], 2u * (unsigned)(t + 1) + (done ? 1u : 0u));
-    }
     if (done) break;
   }
 }
@@ -819,13 +820,11 @@ __global__ void __launch_bounds__(kPairThreads, 2)
         atomicMax(&a.phases->loop_max, tn);
       }
     }
-    // arrival: this CTA's row sums are in (the fence orders every thread's
-    // additions, seen through the block barrier, before the count)
+    // arrival: this CTA's row sums are in (the release, cumulative over what
+    // thread 0 has seen through the block barrier, orders every thread's
+    // additions before the count)
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(&a.sync->arrivals, 1u);
-    }
+    if (threadIdx.x == 0) red_release_add_u32(&a.sync->arrivals, 1u);
   }
   // tiles issued ahead for steps that did not run: let them land
   if (threadIdx.x == 0)

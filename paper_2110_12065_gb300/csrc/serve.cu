@@ -3,8 +3,8 @@
 // thread per context owns a private child context (its own stream and
 // scratch).  Every admitted request gets its matrix built on the device (C
 // by Eq. (5), or G by Eq. (11)) and its iterate kept resident; each round
-// advances every resident solve by up to kRoundSteps steps of Alg. 1 (to the
-// end of its current component when no request is waiting for admission)
+// advances every resident solve by up to kRoundSteps steps of Alg. 1 (up to
+// kLongRoundSteps, a whole component, when no request waits for admission)
 // in one persistent batched launch per (storage, op), then deflates finished
 // PCA components (Alg. 2 step 6) or copies finished results to the caller.
 #include <algorithm>
@@ -21,6 +21,9 @@ namespace mapi {
 
 using Clock = std::chrono::steady_clock;
 constexpr int kRoundSteps = 25;
+// a round with nobody waiting for admission: one PCA component, and a bound
+// on how long a cancellation waits
+constexpr int kLongRoundSteps = 100;
 constexpr int kMaxComponents = 8;
 // Solves this large iterate on the whole GPU (the split GEMV, one launch per
 // step) instead of a share of the batched launch: one cluster per instance
@@ -363,7 +366,8 @@ void run_round(Server* sv) {
   }
   auto steps_of = [waiting](const ServeReq* q) {
     const int rem = q->r.max_iters - q->it_comp;
-    return (!waiting || rem < kRoundSteps) ? rem : kRoundSteps;
+    const int cap = waiting ? kRoundSteps : kLongRoundSteps;
+    return rem < cap ? rem : cap;
   };
   // deflations and copies that ended the previous round ran on the loop's
   // stream: the batched launches of this round come after them
