@@ -49,7 +49,7 @@ constexpr int kPairMaxStream = 96;            // streaming clusters at most
 struct PairSync {
   unsigned arrivals;           // streaming CTAs that finished a step, all steps
   int err;                     // a bounded wait ran out somewhere
-  unsigned pub[kPairCluster];  // epilogue CTA r: 2 x (steps published) + stop bit
+  unsigned pad_[kPairCluster];
   unsigned xmax;               // max |X| as FP32 bits (the fixed-point scale)
 };
 
@@ -73,6 +73,7 @@ struct PairSolveArgs {
   long long stall_ns;  // > 0: fault-detection test (mapi_debug_stall)
   PairPhases* phases;  // non-null: phase stamps (mapi_pair_phases)
   float* raw_out;      // non-null: one step, its y (no deflation or norm) written here
+  unsigned long long* wpub;  // [D_pad] the published iterate: value bits | tag << 32
 };
 
 template <int ST>
@@ -103,6 +104,26 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 }
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+// Bounded spin until the tag (high word) of *p is >= tag; the word, or 0
+// when the limit ran out.
+__device__ unsigned long long wait_tag(const unsigned long long* p, unsigned tag) {
+  long long t0 = 0;
+  for (int i = 0;; ++i) {
+    const unsigned long long v = ld_acquire_u64(p);
+    if ((unsigned)(v >> 32) >= tag) return v;
+    if (i == 0) t0 = globaltimer_ns();
+    else if (globaltimer_ns() - t0 > kWaitLimitNs) return 0;
+    if (i > 4096) __nanosleep(32);
+  }
 }
 __device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -270,14 +291,23 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
     // 2. y = (sum of the fixed-point row sums) 2^-s / denom, all rows (each
     //    copy and row read once; the integer sum is exact)
     unsigned long long* accb = a.acc + (size_t)(t & 1) * kAccCopies * D_pad;
-    for (int i = threadIdx.x; i < D_pad; i += NT) {
-      long long v[kAccCopies];
+    {
+      // D_pad = 4 RS rows, RS / 64 per thread: every load in flight at once
+      constexpr int PER = 4 * RS / NT;
+      long long v[PER][kAccCopies];
 #pragma unroll
-      for (int c = 0; c < kAccCopies; ++c) v[c] = (long long)__ldcg(accb + (size_t)c * D_pad + i);
-      long long s = 0;
+      for (int k = 0; k < PER; ++k)
 #pragma unroll
-      for (int c = 0; c < kAccCopies; ++c) s += v[c];
-      yfull[i] = i < D ? __ll2float_rn(s) * inv / a.denom : 0.f;
+        for (int c = 0; c < kAccCopies; ++c)
+          v[k][c] = (long long)__ldcg(accb + (size_t)c * D_pad + threadIdx.x + k * NT);
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x + k * NT;
+        long long s = 0;
+#pragma unroll
+        for (int c = 0; c < kAccCopies; ++c) s += v[k][c];
+        yfull[i] = i < D ? __ll2float_rn(s) * inv / a.denom : 0.f;
+      }
     }
     for (int i = threadIdx.x; i < 2 * D_pad; i += NT) cbuf[i] = 0.f;
     __syncthreads();
@@ -292,11 +322,6 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
         st->done = 1;
         if (*(volatile const int*)&a.sync->err) st->status = MAPI_ETIMEOUT;
         a.ctl->all_done = 1;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        st_release_u32(&a.sync->pub[r], 3u);
       }
       break;
     }
@@ -574,9 +599,12 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
     }
     // 6. publish this CTA's rows (and the stop bit) to the streaming CTAs of
     //    the same rank
-    __syncthreads();
-    if (threadIdx.x == 0)
-      st_release_u32(&a.sync->pub[r], 2u * (unsigned)(t + 1) + (done ? 1u : 0u));
+    // each thread publishes its rows: value and tag 2 (t + 1) + stop in one
+    // 64-bit word, released after this thread's writes of the step (its
+    // rows of the iterate and of the cleared accumulator)
+    const unsigned long long tag = (unsigned long long)(2u * (unsigned)(t + 1) + (done ? 1u : 0u));
+    for (int i = threadIdx.x; i < RS; i += NT)
+      st_release_u64(a.wpub + r0 + i, (tag << 32) | __float_as_uint(wo[i]));
     if (done) break;
   }
 }
@@ -737,30 +765,42 @@ __global__ void __launch_bounds__(kPairThreads, 2)
   unsigned gbase = 0;  // global index of this step's first tile
   for (int t = 0; t < a.T; ++t) {
     if (t > 0) {
-      // the epilogue's rows of w_t for this rank (and whether to stop)
-      if (threadIdx.x == 0) {
-        const unsigned v = wait_geq(&a.sync->pub[crank], 2u * (unsigned)t);
-        if (v == 0) {
+      // the epilogue's rows of w_t for this rank, each in a tagged word
+      // (and whether to stop, the tag's low bit): thread 0 waits for the
+      // first row, then every thread takes its own (already there, or soon)
+      if (threadIdx.x == 0 && wait_tag(a.wpub + (int)crank * RC, 2u * (unsigned)t) == 0ull) {
+        s_err = 1;
+        atomicExch(&a.sync->err, 1);
+        s_stop = 1;
+      }
+      __syncthreads();
+      for (int r = threadIdx.x; r < RC && !s_stop; r += blockDim.x) {
+        const unsigned long long v = wait_tag(a.wpub + (int)crank * RC + r, 2u * (unsigned)t);
+        if (v == 0ull) {
           s_err = 1;
           atomicExch(&a.sync->err, 1);
           s_stop = 1;
-        } else if (v & 1u) {
-          s_stop = 1;
+        } else {
+          if ((v >> 32) & 1ull) s_stop = 1;
+          const auto p = Op<OP>::prep(__uint_as_float((unsigned)v));
+          if constexpr (OP == MAPI_OP_DOT) wp[r] = make_float4(p.w, 0.f, 0.f, 0.f);
+          else wp[r] = make_float4(p.lo, p.hi, p.s, 0.f);
         }
       }
       __syncthreads();
       if (s_stop) break;
+    } else {
+      // w_0 from the start kernel
+      for (int r = threadIdx.x; r < RC; r += blockDim.x) {
+        const int d = (int)crank * RC + r;
+        const float wv = d < a.D ? __ldcg(a.wb0 + d) : 0.f;
+        const auto p = Op<OP>::prep(wv);
+        if constexpr (OP == MAPI_OP_DOT) wp[r] = make_float4(p.w, 0.f, 0.f, 0.f);
+        else wp[r] = make_float4(p.lo, p.hi, p.s, 0.f);
+      }
+      __syncthreads();
     }
     if (a.phases && threadIdx.x == 0) atomicMin(&a.phases->start_min, gtimer_u64());
-    const float* w = (t & 1) ? a.wb1 : a.wb0;
-    for (int r = threadIdx.x; r < RC; r += blockDim.x) {
-      const int d = (int)crank * RC + r;
-      const float wv = d < a.D ? __ldcg(w + d) : 0.f;
-      const auto p = Op<OP>::prep(wv);
-      if constexpr (OP == MAPI_OP_DOT) wp[r] = make_float4(p.w, 0.f, 0.f, 0.f);
-      else wp[r] = make_float4(p.lo, p.hi, p.s, 0.f);
-    }
-    __syncthreads();
 #pragma unroll
     for (int j = 0; j < RW; ++j) acc[j] = 0.f;
     // two tiles in flight: A(j) overlaps the cluster exchange of tile j - 1
@@ -982,8 +1022,10 @@ mapi_status plan_pair(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, PairPlan* pl
   return MAPI_OK;
 }
 
+// Scratch: accumulators [2][kAccCopies][D_pad], the published iterate
+// [D_pad] (both 64-bit words), then PairSync.
 size_t pair_scratch_bytes(const PairPlan& pl) {
-  return sizeof(unsigned long long) * 2 * kAccCopies * (size_t)pl.D_pad + 256;
+  return sizeof(unsigned long long) * (2 * kAccCopies + 1) * (size_t)pl.D_pad + 256;
 }
 
 mapi_status launch_pair_prepare(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
@@ -992,7 +1034,7 @@ mapi_status launch_pair_prepare(mapi_ctx* ctx, cudaStream_t s, const PairPlan& p
   // accumulators and the shared state, then find max |X| (once per solve)
   MAPI_CUDA_TRY(ctx, cudaMemsetAsync(scratch, 0, pair_scratch_bytes(pl), s));
   PairSync* sync = reinterpret_cast<PairSync*>(
-      (char*)scratch + sizeof(unsigned long long) * 2 * kAccCopies * (size_t)pl.D_pad);
+      (char*)scratch + sizeof(unsigned long long) * (2 * kAccCopies + 1) * (size_t)pl.D_pad);
   const int64_t elems = (int64_t)X->rows_pad * X->ld;
   const int blocks = 4 * ctx->sm_count;
   if (X->storage == MAPI_ST_F32)
@@ -1023,7 +1065,7 @@ mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
   const int64_t nmine_max = (ntiles + pl.clusters - 2) / (pl.clusters - 1);
   if ((int64_t)T * nmine_max >= (1ll << 31))
     return fail(ctx, MAPI_EINVAL, "pair mode: max_iters x column tiles per cluster >= 2^31");
-  const size_t acc_bytes = sizeof(unsigned long long) * 2 * kAccCopies * (size_t)pl.D_pad;
+  const size_t acc_bytes = sizeof(unsigned long long) * (2 * kAccCopies + 1) * (size_t)pl.D_pad;
   PairSync* sync = reinterpret_cast<PairSync*>((char*)scratch + acc_bytes);
   // the accumulators and the shared state of the launch start at zero (max
   // |X| is kept)
@@ -1049,6 +1091,7 @@ mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
   a.stall_ns = ctx->stall_ns;
   a.phases = ctx->phases_on ? (PairPhases*)ctx->pair_phases.p : nullptr;
   a.raw_out = raw_out;
+  a.wpub = reinterpret_cast<unsigned long long*>(scratch) + 2 * kAccCopies * (size_t)pl.D_pad;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
