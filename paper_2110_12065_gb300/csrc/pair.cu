@@ -212,7 +212,7 @@ __host__ __device__ constexpr int pair_epi_floats(int rc, int d_pad) {
 // the projection for DOT; CTA r's warp group g owns the earlier components
 // m = r + 4 g (mod 8)), w' = u / ||u||, the stop test, and the publication
 // of CTA r's rows of w' to the streaming CTAs of rank r.
-template <int RS>
+template <int RS, int OP>
 __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster, float* fsh,
                               int s_exp) {
   constexpr int CS = kPairCluster;
@@ -232,8 +232,9 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
   __shared__ float red[33];
   __shared__ float part[8];
   __shared__ float gtot[2][4][8];
-  const bool dot = a.defl.op == MAPI_OP_DOT;
-  const bool two = a.defl.op == MAPI_OP_MIN2;
+  // the deflation's operator is the iteration's (DeflArgs::op == OP)
+  constexpr bool dot = OP == MAPI_OP_DOT;
+  constexpr bool two = OP == MAPI_OP_MIN2;
   const int nprev = a.defl.nprev;
   // with at most 8 earlier components each group's arrays stay resident
   const bool resident = nprev <= 2 * CS;
@@ -347,7 +348,7 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
           load_comp(m, g, tg, 128);
         }
         group_bar(g);
-        if (dot) {
+        if constexpr (dot) {
           TwoSum pd;
           for (int i = tg; i < D; i += 128) pd.add_prod(wm_s[i], yfull[i]);
 #pragma unroll
@@ -380,19 +381,23 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
         // min2, c y and y
         const int p0 = wq * 256 + lane * 8;
         TwoSum la, lb, la2, lb2;  // this lane's totals
+        float kc[8], kz[8], ky[8];  // the positions' c, z and y, kept for the second walk
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int p = p0 + k;
-          if (p < D) {
-            const int i = perm_s[dpad(p)];
-            const float y = yfull[i];
-            const float c = cs_s[dpad(p)];
-            const float z = sgnf(wm_s[i]) * y;
-            la.add_prod(c, z);
-            lb.add(z);
-            if (two) {
-              la2.add_prod(c, y);
-              lb2.add(y);
+          const int i = p < D ? perm_s[dpad(p)] : 0;
+          ky[k] = p < D ? yfull[i] : 0.f;
+          kc[k] = p < D ? cs_s[dpad(p)] : 0.f;
+          kz[k] = p < D ? sgnf(wm_s[i]) * ky[k] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if (p0 + k < D) {
+            la.add_prod(kc[k], kz[k]);
+            lb.add(kz[k]);
+            if constexpr (two) {
+              la2.add_prod(kc[k], ky[k]);
+              lb2.add(ky[k]);
             }
           }
         }
@@ -408,7 +413,7 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
         for (int o = 1; o < 32; o <<= 1) {
           up(ia, o);
           up(ib, o);
-          if (two) {
+          if constexpr (two) {
             up(ia2, o);
             up(ib2, o);
           }
@@ -452,13 +457,13 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
           if (q < wq) {
             oa.add(ea);
             ob.add(eb);
-            if (two) {
+            if constexpr (two) {
               oa2.add(ea2);
               ob2.add(eb2);
             }
           }
           totB.add(eb);
-          if (two) totB2.add(eb2);
+          if constexpr (two) totB2.add(eb2);
         }
         // walk the lane's positions again from its offset: A_p, and the
         // suffix S_p = totB - B_p, each rounded once
@@ -466,17 +471,14 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
         for (int k = 0; k < 8; ++k) {
           const int p = p0 + k;
           if (p < D) {
-            const int i = perm_s[dpad(p)];
-            const float y = yfull[i];
-            const float c = cs_s[dpad(p)];
-            const float z = sgnf(wm_s[i]) * y;
+            const float y = ky[k], c = kc[k], z = kz[k];
             oa.add_prod(c, z);
             ob.add(z);
             TwoSum sb = totB;
             sb.add(neg(ob));
             sA[dpad(p)] = oa.value();
             sS[dpad(p)] = sb.value();
-            if (two) {
+            if constexpr (two) {
               oa2.add_prod(c, y);
               ob2.add(y);
               TwoSum sb2 = totB2;
@@ -487,12 +489,38 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
           }
         }
         group_bar(g);
-        for (int i = tg; i < D; i += 128) {
-          const float wi = wm_s[i], ci = fabsf(wi);
-          const int q = dpad(ub_s[i]);
-          float v = sgnf(wi) * fmaf(ci, sS[q], sA[q]);
-          if (two) v = 0.5f * (v + fmaf(ci, sS2[q], sA2[q]));
-          cb[i] += v;
+        {
+          // outputs i = tg + 128 k (D <= 1024: at most 8 per thread), each
+          // stage's loads issued for all k before the next stage uses them
+          constexpr int PO = kDeflMaxD / 128;
+          float wi[PO];
+          int qi[PO];
+#pragma unroll
+          for (int k = 0; k < PO; ++k) {
+            const int i = tg + 128 * k;
+            wi[k] = i < D ? wm_s[i] : 0.f;
+            qi[k] = i < D ? dpad(ub_s[i]) : 0;
+          }
+          float va[PO], vs[PO], va2[PO], vs2[PO];
+#pragma unroll
+          for (int k = 0; k < PO; ++k) {
+            va[k] = sA[qi[k]];
+            vs[k] = sS[qi[k]];
+            if constexpr (two) {
+              va2[k] = sA2[qi[k]];
+              vs2[k] = sS2[qi[k]];
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < PO; ++k) {
+            const int i = tg + 128 * k;
+            if (i < D) {
+              const float ci = fabsf(wi[k]);
+              float v = sgnf(wi[k]) * fmaf(ci, vs[k], va[k]);
+              if constexpr (two) v = 0.5f * (v + fmaf(ci, vs2[k], va2[k]));
+              cb[i] += v;
+            }
+          }
         }
       }
     }
@@ -664,7 +692,7 @@ __global__ void __launch_bounds__(kPairThreads, 2)
   const int s_exp = acc_scale_exp(__uint_as_float(*(volatile const unsigned*)&a.sync->xmax),
                                   a.ncols, a.D_pad, dot);
   if (cid == a.nstream) {
-    pair_epilogue<RC>(a, cluster, reinterpret_cast<float*>(stage), s_exp);
+    pair_epilogue<RC, OP>(a, cluster, reinterpret_cast<float*>(stage), s_exp);
     cluster.sync();  // peers may still read this CTA's shared memory until here
     return;
   }
