@@ -370,8 +370,9 @@ def run_variants(M, ctx, torch, dev, X, W0d, peaks):
             "ms_per_solve": round(ms, 3), "iters_per_s": round(K_COMP * ITERS / (ms / 1e3), 1),
             "build_ms": round(mc["ms"] / max(1, mc["launches"]), 3),
             "build_terms_per_s": round(mc["terms"] / (mc["ms"] / 1e3), 1) if mc["ms"] else None,
+            # the build widens BF16 while staging: its inner loop is the FP32 term
             "build_alu_frac": round(mc["terms"] / (mc["ms"] / 1e3) / alu_peak_terms(
-                probe["min1_term_f32"] if stg == "f32" else probe["min1_term_bf16"]), 4)
+                probe["min1_term_f32"]), 4)
             if mc["ms"] else None,
             "iterate_us_per_step": round(gv["ms"] / max(1, gv["launches"]) * 1e3, 3)}
 
@@ -392,8 +393,9 @@ def run_variants(M, ctx, torch, dev, X, W0d, peaks):
         elems = float((sizes.astype(np.float64) ** 2).sum())
         terms = elems * 4 * steps
         eb = 4 if stg == "f32" else 2
+        # each BF16 element is widened once for the four vectors
         peak_terms = alu_peak_terms(probe["min1_term_f32"] if stg == "f32"
-                                    else probe["min1_term_bf16"])
+                                    else probe["min1_term_bf16_x4"])
         out[f"batched_{n_inst}x4_{stg}"] = {
             "instances": n_inst, "steps": steps,
             "instance_steps_per_s": round(n_inst * steps / (ms / 1e3), 1),

@@ -445,7 +445,9 @@ mapi_status mapi_pair_phases(mapi_ctx* ctx, int enable, double* out_us);
  *   mix 0: FP32 min1 terms, sign(w) clamp(a, -|w|, |w|) accumulated by a
  *          fused multiply-add by +-1 (2 min/max + 1 FMA);
  *   mix 1: FMA instructions;  mix 2: min/max instructions;
- *   mix 3: min1 terms on a BF16 operand widened to FP32 (1 shift + the term).
+ *   mix 3: min1 terms on a BF16 operand widened to FP32 (1 shift + the term);
+ *   mix 4: min1 terms on BF16 operands each widened once for four vectors
+ *          (the batched kernel's mix with four start vectors).
  * Per thread-lane counts; clock-independent.  Synchronous. */
 mapi_status mapi_alu_probe(mapi_ctx* ctx, int mix, double* per_clock_per_sm);
 

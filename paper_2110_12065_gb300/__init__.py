@@ -474,7 +474,7 @@ def mapi_pair_phases(ctx, enable: bool = True) -> dict:
     return {k: float(v) for k, v in zip(PAIR_PHASES, out)}
 
 
-ALU_MIXES = ("min1_term_f32", "ffma", "fmnmx", "min1_term_bf16")
+ALU_MIXES = ("min1_term_f32", "ffma", "fmnmx", "min1_term_bf16", "min1_term_bf16_x4")
 
 
 def mapi_alu_probe(ctx, mix) -> float:

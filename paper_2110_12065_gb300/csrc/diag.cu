@@ -17,7 +17,8 @@ constexpr int kProbeIters = 4096;
 // mix 0: the FP32 min1 term, sign(w) clamp(a, -|w|, |w|) added by a fused
 //        multiply-add by +-1 (two min/max and one FMA per term);
 // mix 1: FMA alone;  mix 2: min/max alone (two per update);
-// mix 3: the min1 term on a BF16 operand widened to FP32 first.
+// mix 3: the min1 term on a BF16 operand widened to FP32 first;
+// mix 4: the same, each widened element used against four vectors' bounds.
 // Each update of chain j reads chain j + 1, so nothing can be hoisted.
 template <int MIX>
 __global__ void __launch_bounds__(kProbeThreads)
@@ -39,6 +40,16 @@ __global__ void __launch_bounds__(kProbeThreads)
       if (MIX == 3) {
         const float x = __uint_as_float(__float_as_uint(a) << 16);
         acc[j] = fmaf(fminf(fmaxf(x, lo), hi), sg, acc[j]);
+      }
+      if (MIX == 4 && (j & 3) == 0) {
+        // one BF16 element widened once and used against four vectors'
+        // bounds (the batched kernel's four start vectors)
+        const float x = __uint_as_float(__float_as_uint(a) << 16);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float b = 0.25f * (float)(v + 1);
+          acc[j + v] = fmaf(fminf(fmaxf(x, -b), b), sg, acc[j + v]);
+        }
       }
     }
   }
@@ -65,13 +76,14 @@ mapi_status run_probe(mapi_ctx* ctx, long long* dcyc, float* dsink, int blocks) 
 using namespace mapi;
 
 extern "C" mapi_status mapi_alu_probe(mapi_ctx* ctx, int mix, double* per_clock_per_sm) {
-  if (!ctx || !per_clock_per_sm || mix < 0 || mix > 3) return MAPI_EINVAL;
+  if (!ctx || !per_clock_per_sm || mix < 0 || mix > 4) return MAPI_EINVAL;
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != ctx->device) cudaSetDevice(ctx->device);
   int per_sm = 0;
-  const void* fns[4] = {(const void*)k_alu_probe<0>, (const void*)k_alu_probe<1>,
-                        (const void*)k_alu_probe<2>, (const void*)k_alu_probe<3>};
+  const void* fns[5] = {(const void*)k_alu_probe<0>, (const void*)k_alu_probe<1>,
+                        (const void*)k_alu_probe<2>, (const void*)k_alu_probe<3>,
+                        (const void*)k_alu_probe<4>};
   mapi_status st = MAPI_OK;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[mix], kProbeThreads, 0) !=
           cudaSuccess ||
@@ -91,7 +103,8 @@ extern "C" mapi_status mapi_alu_probe(mapi_ctx* ctx, int mix, double* per_clock_
       st = mix == 0   ? run_probe<0>(ctx, dcyc, dsink, blocks)
            : mix == 1 ? run_probe<1>(ctx, dcyc, dsink, blocks)
            : mix == 2 ? run_probe<2>(ctx, dcyc, dsink, blocks)
-                      : run_probe<3>(ctx, dcyc, dsink, blocks);
+           : mix == 3 ? run_probe<3>(ctx, dcyc, dsink, blocks)
+                      : run_probe<4>(ctx, dcyc, dsink, blocks);
     std::vector<long long> h(blocks);
     if (st == MAPI_OK) {
       if (cudaMemcpyAsync(h.data(), dcyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost,
