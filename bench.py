@@ -284,6 +284,40 @@ def run_gpu(args, rank, world, local_rank, dist):
     return line
 
 
+def batched_leg(M, ctx, torch, dev, probe, hbm, stg, n_inst=4096, steps=100):
+    """The batched workload: Wishart instances A = W W^T / k (n log-uniform in
+    [64, 2048], k = n/2), 4 start vectors each, 100 steps, one persistent
+    launch; ALU fraction against the probe's rate of the kernel's mix."""
+    import datagen
+    sizes = datagen.wishart_sizes(n_inst, seed=0)
+    mats, items = [], []
+    for k, n in enumerate(sizes):
+        mats.append(M.mapi_matrix_upload(ctx, datagen.wishart_instance_device(int(n), k), stg))
+        w0 = torch.from_numpy(np.stack([datagen.start_vector(int(n), seed=10 * k + v)
+                                        for v in range(4)])).to(dev)
+        items.append((mats[-1], w0, torch.empty_like(w0)))
+    try:
+        r = M.mapi_autotune_batched(ctx, items, "min1", 4, iters=2)
+        run = lambda: M.mapi_iterate_batched(ctx, items, "min1", 4, steps)
+        ms = timed(torch, run, 1)
+    finally:
+        for m in mats:
+            M.mapi_matrix_free(ctx, m)
+    elems = float((sizes.astype(np.float64) ** 2).sum())
+    terms = elems * 4 * steps
+    eb = 4 if stg == "f32" else 2
+    # each BF16 element is widened once for the four vectors
+    peak_terms = alu_peak_terms(probe["min1_term_f32"] if stg == "f32"
+                                else probe["min1_term_bf16_x4"])
+    return {"instances": n_inst, "steps": steps,
+            "instance_steps_per_s": round(n_inst * steps / (ms / 1e3), 1),
+            "ms_per_launch": round(ms, 3), "rows_per_warp": r,
+            "terms_per_s": round(terms / (ms / 1e3), 1),
+            "alu_frac": round(terms / (ms / 1e3) / peak_terms, 4),
+            "matrix_gbs": round(elems * eb * steps / (ms / 1e3) / 1e9, 1),
+            "hbm_frac": round(elems * eb * steps / (ms / 1e3) / 1e9 / hbm, 4)}
+
+
 def pair_phases(M, ctx, Xd, W0d, P, storage="f32"):
     """Where the time of a pair step goes: the headline solve run once with
     the kernel's %globaltimer phase stamps on (microseconds per step,
@@ -376,36 +410,8 @@ def run_variants(M, ctx, torch, dev, X, W0d, peaks):
             if mc["ms"] else None,
             "iterate_us_per_step": round(gv["ms"] / max(1, gv["launches"]) * 1e3, 3)}
 
-    # batched: 4096 Wishart instances, n log-uniform in [64, 2048], 4 start
-    # vectors each, 100 steps, one persistent launch (the batched workload)
-    n_inst, steps = 4096, 100
-    sizes = datagen.wishart_sizes(n_inst, seed=0)
     for stg in ("f32", "bf16"):
-        mats, items = [], []
-        for k, n in enumerate(sizes):
-            mats.append(M.mapi_matrix_upload(ctx, datagen.wishart_instance_device(int(n), k), stg))
-            w0 = torch.from_numpy(np.stack([datagen.start_vector(int(n), seed=10 * k + v)
-                                            for v in range(4)])).to(dev)
-            items.append((mats[-1], w0, torch.empty_like(w0)))
-        r = M.mapi_autotune_batched(ctx, items, "min1", 4, iters=2)
-        run = lambda: M.mapi_iterate_batched(ctx, items, "min1", 4, steps)
-        ms = timed(torch, run, 1)
-        elems = float((sizes.astype(np.float64) ** 2).sum())
-        terms = elems * 4 * steps
-        eb = 4 if stg == "f32" else 2
-        # each BF16 element is widened once for the four vectors
-        peak_terms = alu_peak_terms(probe["min1_term_f32"] if stg == "f32"
-                                    else probe["min1_term_bf16_x4"])
-        out[f"batched_{n_inst}x4_{stg}"] = {
-            "instances": n_inst, "steps": steps,
-            "instance_steps_per_s": round(n_inst * steps / (ms / 1e3), 1),
-            "ms_per_launch": round(ms, 3), "rows_per_warp": r,
-            "terms_per_s": round(terms / (ms / 1e3), 1),
-            "alu_frac": round(terms / (ms / 1e3) / peak_terms, 4),
-            "matrix_gbs": round(elems * eb * steps / (ms / 1e3) / 1e9, 1),
-            "hbm_frac": round(elems * eb * steps / (ms / 1e3) / 1e9 / hbm, 4)}
-        for m in mats:
-            M.mapi_matrix_free(ctx, m)
+        out[f"batched_4096x4_{stg}"] = batched_leg(M, ctx, torch, dev, probe, hbm, stg)
 
     # plain MAPI / RPI on the n = 512 symmetric Gaussian, 200 steps
     A = datagen.symmetric_gaussian(512, seed=0).astype(np.float32)
@@ -1080,6 +1086,11 @@ def run_case(case: str):
         out = f"{case}: {Nn} images of {side}x{side}, {k} components, iters {its}"
     elif case == "oracle-times":
         out = json.dumps({"case": case, "oracle": oracle_times()})
+    elif case == "batched":
+        probe = alu_probe(M, ctx)
+        hbm = measured_peaks()["hbm_gbs"]
+        out = json.dumps({"case": case, **{stg: batched_leg(M, ctx, torch, "cuda", probe, hbm, stg)
+                                           for stg in ("f32", "bf16")}})
     elif case == "alu-peak":
         out = json.dumps({"case": case, "per_clk_per_sm": alu_probe(M, ctx)})
     elif case == "minibatch":
@@ -1091,17 +1102,26 @@ def run_case(case: str):
         out = f"{case}: 10^6 x 10, 100 steps of 1000"
     elif case == "serve":
         out = json.dumps(run_serving_config5(M, torch, "cuda"))
-    elif case == "batched-f32":
+    elif case in ("batched-f32", "batched-bf16"):
+        # 512 instances of the batched workload, autotuned as the benchmark
+        # is; only the measured launch lies inside the profiler range
+        stg = case.split("-")[1]
         sizes = datagen.wishart_sizes(512, seed=0)
         items, mats = [], []
         for k, n in enumerate(sizes):
-            mats.append(M.mapi_matrix_upload(ctx, datagen.wishart_instance_device(int(n), k), "f32"))
+            mats.append(M.mapi_matrix_upload(ctx, datagen.wishart_instance_device(int(n), k), stg))
             w0 = torch.rand(4, int(n), device="cuda") * 2 - 1
             items.append((mats[-1], w0, torch.empty_like(w0)))
-        it, _, _ = M.mapi_iterate_batched(ctx, items, "min1", 4, 3)
+        r = M.mapi_autotune_batched(ctx, items, "min1", 4, iters=2)
+        M.mapi_iterate_batched(ctx, items, "min1", 4, 3)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        M.mapi_iterate_batched(ctx, items, "min1", 4, 3)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
         for m in mats:
             M.mapi_matrix_free(ctx, m)
-        out = f"{case}: 512 instances x 4 vectors, 3 steps"
+        out = f"{case}: 512 instances x 4 vectors, 3 steps, rows per warp {r}"
     else:
         raise SystemExit(f"unknown case {case}")
     torch.cuda.synchronize()
