@@ -1086,6 +1086,29 @@ def run_case(case: str):
         out = f"{case}: {Nn} images of {side}x{side}, {k} components, iters {its}"
     elif case == "oracle-times":
         out = json.dumps({"case": case, "oracle": oracle_times()})
+    elif case == "gemv":
+        hbm = measured_peaks()["hbm_gbs"]
+        n = 16384
+        ip, ix = datagen.barabasi_albert_digraph(n, m=8, seed=0)
+        dip, dix = torch.from_numpy(ip).cuda(), torch.from_numpy(ix).cuda()
+        w0 = torch.from_numpy(datagen.start_vector(n, seed=0, low=0.0, high=1.0)).cuda()
+        res = {}
+        for stg in ("f32", "bf16", "fp8", "i16"):
+            G = M.mapi_google_matrix(ctx, dip, dix, n, 0.85, stg)
+            run = lambda: M.mapi_iterate(ctx, G, "min1", w0, 100)
+            M.mapi_profile(ctx, True)
+            run()
+            torch.cuda.synchronize()
+            M.mapi_get_stats(ctx, reset=True)
+            run()
+            torch.cuda.synchronize()
+            gv = M.mapi_get_stats(ctx, reset=True)["gemv"]
+            M.mapi_profile(ctx, False)
+            M.mapi_matrix_free(ctx, G)
+            gbs = gv["bytes"] / (gv["ms"] / 1e3) / 1e9
+            res[stg] = {"us_per_step": round(gv["ms"] / gv["launches"] * 1e3, 2),
+                        "gemv_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+        out = json.dumps({"case": case, "pagerank_n16384": res})
     elif case == "batched":
         probe = alu_probe(M, ctx)
         hbm = measured_peaks()["hbm_gbs"]
