@@ -94,6 +94,52 @@ struct PairCols<kBF16> {
   }
 };
 
+// The iterate's (or the column sums') prepared form as the tile loop keeps
+// it: Op's (lo, hi, s) by default; for MIN1 only (w, s), the bounds -|w|
+// and |w| taken at each use (the same values as Op's lo and hi, so the terms
+// are identical), which leaves the register file one value per entry
+// lighter.
+template <int OP>
+struct PairTerm {
+  using P = typename Op<OP>::P;
+  using S = float4;  // shared-memory form
+  static __device__ __forceinline__ S store(float w) {
+    const P p = Op<OP>::prep(w);
+    return make_float4(p.lo, p.hi, p.s, 0.f);
+  }
+  static __device__ __forceinline__ P load(const S& q) { return {q.x, q.y, q.z}; }
+  static __device__ __forceinline__ P prep(float w) { return Op<OP>::prep(w); }
+  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
+    return Op<OP>::term(a, p, acc);
+  }
+};
+template <>
+struct PairTerm<MAPI_OP_MIN1> {
+  struct P {
+    float w, s;
+  };
+  using S = float2;
+  static __device__ __forceinline__ S store(float w) {
+    return make_float2(w, copysignf(1.f, w));
+  }
+  static __device__ __forceinline__ P load(const S& q) { return {q.x, q.y}; }
+  static __device__ __forceinline__ P prep(float w) { return {w, copysignf(1.f, w)}; }
+  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
+    return fmaf(fminf(fmaxf(a, -fabsf(p.w)), fabsf(p.w)), p.s, acc);
+  }
+};
+template <>
+struct PairTerm<MAPI_OP_DOT> {
+  using P = Op<MAPI_OP_DOT>::P;
+  using S = float;
+  static __device__ __forceinline__ S store(float w) { return w; }
+  static __device__ __forceinline__ P load(const S& q) { return {q}; }
+  static __device__ __forceinline__ P prep(float w) { return {w}; }
+  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
+    return fmaf(a, p.w, acc);
+  }
+};
+
 __device__ __forceinline__ unsigned long long gtimer_u64() {
   return (unsigned long long)globaltimer_ns();
 }
@@ -661,7 +707,8 @@ __global__ void __launch_bounds__(kPairThreads, 2)
   // B of tile j)
   __shared__ __align__(8) uint64_t tready[4];
   __shared__ __align__(8) uint64_t never;  // nothing ever arrives here
-  __shared__ float4 wp[RC];                 // (lo, hi, s, 0) per row of this CTA
+  using PT = PairTerm<OP>;
+  __shared__ typename PT::S wp[RC];         // the prepared iterate, per row of this CTA
   __shared__ float tbuf[2][kPairWarps][TC];  // per-warp column partials (by tile parity)
   __shared__ float tin[4][kPairCluster][TC];  // column partials pushed by each CTA
   __shared__ int s_err;
@@ -740,12 +787,9 @@ __global__ void __launch_bounds__(kPairThreads, 2)
     for (int jj = 0; jj < RW; ++jj) {
       float x[CPL];
       PC::get(raw[jj], x);
-      const float4 q = wp[warp * RW + jj];
-      typename Op<OP>::P p;
-      if constexpr (OP == MAPI_OP_DOT) p = {q.x};
-      else p = {q.x, q.y, q.z};
+      const typename PT::P p = PT::load(wp[warp * RW + jj]);
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) tp[c] = Op<OP>::term(x[c], p, tp[c]);
+      for (int c = 0; c < CPL; ++c) tp[c] = PT::term(x[c], p, tp[c]);
     }
 #pragma unroll
     for (int c = 0; c < CPL; ++c) tbuf[par][warp][lane * CPL + c] = tp[c];
@@ -773,20 +817,20 @@ __global__ void __launch_bounds__(kPairThreads, 2)
     const int slot = (int)(g & 3);
     if (!mbar_wait(&tready[slot], (unsigned)((g >> 2) & 1), s_err ? 1000000LL : kWaitLimitNs))
       s_err = 1;
-    typename Op<OP>::P tpar[CPL];
+    typename PT::P tpar[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
       float tt = 0.f;
 #pragma unroll
       for (int q = 0; q < kPairCluster; ++q) tt += tin[slot][q][lane * CPL + c];
-      tpar[c] = Op<OP>::prep(tt);
+      tpar[c] = PT::prep(tt);
     }
 #pragma unroll
     for (int jj = 0; jj < RW; ++jj) {
       float x[CPL];
       PC::get(raw[jj], x);
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) acc[jj] = Op<OP>::term(x[c], tpar[c], acc[jj]);
+      for (int c = 0; c < CPL; ++c) acc[jj] = PT::term(x[c], tpar[c], acc[jj]);
     }
   };
 
@@ -810,9 +854,7 @@ __global__ void __launch_bounds__(kPairThreads, 2)
           s_stop = 1;
         } else {
           if ((v >> 32) & 1ull) s_stop = 1;
-          const auto p = Op<OP>::prep(__uint_as_float((unsigned)v));
-          if constexpr (OP == MAPI_OP_DOT) wp[r] = make_float4(p.w, 0.f, 0.f, 0.f);
-          else wp[r] = make_float4(p.lo, p.hi, p.s, 0.f);
+          wp[r] = PT::store(__uint_as_float((unsigned)v));
         }
       }
       __syncthreads();
@@ -822,9 +864,7 @@ __global__ void __launch_bounds__(kPairThreads, 2)
       for (int r = threadIdx.x; r < RC; r += blockDim.x) {
         const int d = (int)crank * RC + r;
         const float wv = d < a.D ? __ldcg(a.wb0 + d) : 0.f;
-        const auto p = Op<OP>::prep(wv);
-        if constexpr (OP == MAPI_OP_DOT) wp[r] = make_float4(p.w, 0.f, 0.f, 0.f);
-        else wp[r] = make_float4(p.lo, p.hi, p.s, 0.f);
+        wp[r] = PT::store(wv);
       }
       __syncthreads();
     }
