@@ -87,6 +87,52 @@ struct Op<MAPI_OP_DOT> {
   }
 };
 
+// A vector entry's prepared form for loops that keep many of them in
+// registers: Op's (lo, hi, s) by default; for MIN1 only (w, s), the bounds
+// -|w| and |w| taken at each use (the same values as Op's lo and hi, so the
+// terms are identical), one register per entry fewer.  S is the form kept
+// in shared memory.
+template <int OP>
+struct OpReg {
+  using P = typename Op<OP>::P;
+  using S = float4;  // shared-memory form
+  static __device__ __forceinline__ S store(float w) {
+    const P p = Op<OP>::prep(w);
+    return make_float4(p.lo, p.hi, p.s, 0.f);
+  }
+  static __device__ __forceinline__ P load(const S& q) { return {q.x, q.y, q.z}; }
+  static __device__ __forceinline__ P prep(float w) { return Op<OP>::prep(w); }
+  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
+    return Op<OP>::term(a, p, acc);
+  }
+};
+template <>
+struct OpReg<MAPI_OP_MIN1> {
+  struct P {
+    float w, s;
+  };
+  using S = float2;
+  static __device__ __forceinline__ S store(float w) {
+    return make_float2(w, copysignf(1.f, w));
+  }
+  static __device__ __forceinline__ P load(const S& q) { return {q.x, q.y}; }
+  static __device__ __forceinline__ P prep(float w) { return {w, copysignf(1.f, w)}; }
+  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
+    return fmaf(fminf(fmaxf(a, -fabsf(p.w)), fabsf(p.w)), p.s, acc);
+  }
+};
+template <>
+struct OpReg<MAPI_OP_DOT> {
+  using P = Op<MAPI_OP_DOT>::P;
+  using S = float;
+  static __device__ __forceinline__ S store(float w) { return w; }
+  static __device__ __forceinline__ P load(const S& q) { return {q}; }
+  static __device__ __forceinline__ P prep(float w) { return {w}; }
+  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
+    return fmaf(a, p.w, acc);
+  }
+};
+
 // Integer terms (exact): the same clamp identity on INT32.
 template <int OP>
 struct IOp;

@@ -94,52 +94,6 @@ struct PairCols<kBF16> {
   }
 };
 
-// The iterate's (or the column sums') prepared form as the tile loop keeps
-// it: Op's (lo, hi, s) by default; for MIN1 only (w, s), the bounds -|w|
-// and |w| taken at each use (the same values as Op's lo and hi, so the terms
-// are identical), which leaves the register file one value per entry
-// lighter.
-template <int OP>
-struct PairTerm {
-  using P = typename Op<OP>::P;
-  using S = float4;  // shared-memory form
-  static __device__ __forceinline__ S store(float w) {
-    const P p = Op<OP>::prep(w);
-    return make_float4(p.lo, p.hi, p.s, 0.f);
-  }
-  static __device__ __forceinline__ P load(const S& q) { return {q.x, q.y, q.z}; }
-  static __device__ __forceinline__ P prep(float w) { return Op<OP>::prep(w); }
-  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
-    return Op<OP>::term(a, p, acc);
-  }
-};
-template <>
-struct PairTerm<MAPI_OP_MIN1> {
-  struct P {
-    float w, s;
-  };
-  using S = float2;
-  static __device__ __forceinline__ S store(float w) {
-    return make_float2(w, copysignf(1.f, w));
-  }
-  static __device__ __forceinline__ P load(const S& q) { return {q.x, q.y}; }
-  static __device__ __forceinline__ P prep(float w) { return {w, copysignf(1.f, w)}; }
-  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
-    return fmaf(fminf(fmaxf(a, -fabsf(p.w)), fabsf(p.w)), p.s, acc);
-  }
-};
-template <>
-struct PairTerm<MAPI_OP_DOT> {
-  using P = Op<MAPI_OP_DOT>::P;
-  using S = float;
-  static __device__ __forceinline__ S store(float w) { return w; }
-  static __device__ __forceinline__ P load(const S& q) { return {q}; }
-  static __device__ __forceinline__ P prep(float w) { return {w}; }
-  static __device__ __forceinline__ float term(float a, const P& p, float acc) {
-    return fmaf(a, p.w, acc);
-  }
-};
-
 __device__ __forceinline__ unsigned long long gtimer_u64() {
   return (unsigned long long)globaltimer_ns();
 }
@@ -707,7 +661,7 @@ __global__ void __launch_bounds__(kPairThreads, 2)
   // B of tile j)
   __shared__ __align__(8) uint64_t tready[4];
   __shared__ __align__(8) uint64_t never;  // nothing ever arrives here
-  using PT = PairTerm<OP>;
+  using PT = OpReg<OP>;
   __shared__ typename PT::S wp[RC];         // the prepared iterate, per row of this CTA
   __shared__ float tbuf[2][kPairWarps][TC];  // per-warp column partials (by tile parity)
   __shared__ float tin[4][kPairCluster][TC];  // column partials pushed by each CTA
