@@ -84,6 +84,7 @@ struct PairCols<kF32> {
   static __device__ __forceinline__ void get(uint32_t raw, float (&v)[1]) {
     v[0] = __uint_as_float(raw);
   }
+  static __device__ __forceinline__ void get_b(uint32_t raw, float (&v)[1]) { get(raw, v); }
 };
 template <>
 struct PairCols<kBF16> {
@@ -91,6 +92,16 @@ struct PairCols<kBF16> {
   static __device__ __forceinline__ void get(uint32_t raw, float (&v)[2]) {
     v[0] = __uint_as_float(raw << 16);
     v[1] = __uint_as_float(raw & 0xFFFF0000u);
+  }
+  // The same values by byte permutes, for phase B: written differently from
+  // get() so the compiler cannot keep phase A's widened values alive until
+  // phase B (64 floats instead of 32 packed words, which spilled).
+  static __device__ __forceinline__ void get_b(uint32_t raw, float (&v)[2]) {
+    uint32_t lo, hi;
+    asm("prmt.b32 %0, %1, %2, 0x1044;" : "=r"(lo) : "r"(raw), "r"(0u));
+    asm("prmt.b32 %0, %1, %2, 0x3244;" : "=r"(hi) : "r"(raw), "r"(0u));
+    v[0] = __uint_as_float(lo);
+    v[1] = __uint_as_float(hi);
   }
 };
 
@@ -782,7 +793,7 @@ __global__ void __launch_bounds__(kPairThreads, 2)
 #pragma unroll
     for (int jj = 0; jj < RW; ++jj) {
       float x[CPL];
-      PC::get(raw[jj], x);
+      PC::get_b(raw[jj], x);
 #pragma unroll
       for (int c = 0; c < CPL; ++c) acc[jj] = PT::term(x[c], tpar[c], acc[jj]);
     }
