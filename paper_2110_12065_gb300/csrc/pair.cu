@@ -243,6 +243,15 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
   __shared__ float red[33];
   __shared__ float part[8];
   __shared__ float gtot[2][4][8];
+  // each CTA pushes its norm partial and error flag into every CTA's nin
+  // (st.async, counted by nbar) instead of a cluster barrier and remote reads
+  __shared__ __align__(8) uint64_t nbar;
+  __shared__ float nin[2][CS];
+  if (threadIdx.x == 0) {
+    mbar_init(&nbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();  // no peer pushes before the first step's cluster barrier
   // the deflation's operator is the iteration's (DeflArgs::op == OP)
   constexpr bool dot = OP == MAPI_OP_DOT;
   constexpr bool two = OP == MAPI_OP_MIN2;
@@ -569,19 +578,33 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
       k.add(a.norm_l2 ? x * x : fabsf(x));
     }
     const float np = block_sum<NT>(k.value(), red);
+    // a CTA pushes its partial only after its combine above has read every
+    // peer's cbuf, so once all partials are in, no peer reads this CTA's
+    // cbuf any more (it is cleared again at the next step)
     if (threadIdx.x == 0) {
-      part[0] = np;
-      part[1] = *(volatile const int*)&a.sync->err ? 1.f : 0.f;
+      const float ef = *(volatile const int*)&a.sync->err ? 1.f : 0.f;
+      mbar_expect_tx(&nbar, 2 * CS * 4);
+      const uint32_t bar = smem_u32(&nbar);
+#pragma unroll
+      for (int q = 0; q < CS; ++q) {
+        st_async_f32(mapa_u32(smem_u32(&nin[0][r]), q), np, mapa_u32(bar, q));
+        st_async_f32(mapa_u32(smem_u32(&nin[1][r]), q), ef, mapa_u32(bar, q));
+      }
+      const bool in = mbar_wait(&nbar, (unsigned)(t & 1), kWaitLimitNs);
+      if (!in) atomicExch(&a.sync->err, 1);
+      // in rank order, as (r0 + r1) + (r2 + r3)
+      part[4] = (nin[0][0] + nin[0][1]) + (nin[0][2] + nin[0][3]);
+      part[5] = !in || (nin[1][0] + nin[1][1]) + (nin[1][2] + nin[1][3]) > 0.f ? 1.f : 0.f;
     }
-    cluster.sync();  // also: peers have finished reading this CTA's cbuf
-    const float2 Le = cluster_sum2(cluster, &part[0], &part[4]);
-    float L = Le.x;
-    const bool err = Le.y > 0.f;
+    __syncthreads();
+    float L = part[4];
+    const bool err = part[5] > 0.f;
     if (a.norm_l2) L = sqrtf(L);
     const bool ok = (L > 0.f) && isfinite(L);
     // 5. normalise own rows (the n divisions of §2.2), the delta when a stop
-    //    rule needs it
-    float* wn = (t & 1) ? a.wb0 : a.wb1;
+    //    rule needs it; the iterate stays in shared memory (the streaming
+    //    CTAs take it from the publication below) and goes to global memory
+    //    only after the last step
     Kahan dk;
     if (ok) {
       for (int i = threadIdx.x; i < RS; i += NT) {
@@ -589,7 +612,6 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
         if (d >= D) continue;
         const float x = u[i] / L;
         if (want_delta) dk.add(fabsf(x - wo[i]));
-        wn[d] = x;
         wo[i] = x;
       }
     }
@@ -601,6 +623,14 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
       Dsum = cluster_sum(cluster, &part[2], &part[6]);
     }
     const bool done = !ok || err || (want_delta && Dsum < a.ctl->tol) || t + 1 == a.T;
+    if (done) {
+      // the final iterate where the finish kernel reads it (by the parity of
+      // the steps taken: this step's, or, when the norm failed, the last good
+      // iterate under the previous step's parity)
+      float* wfin = ok ? ((t & 1) ? a.wb0 : a.wb1) : ((t & 1) ? a.wb1 : a.wb0);
+      for (int i = threadIdx.x; i < RS; i += NT)
+        if (r0 + i < D) wfin[r0 + i] = wo[i];
+    }
     if (r == 0 && threadIdx.x == 0) {
       VecState* st = &a.ctl->v[0];
       if (!ok) {
