@@ -329,9 +329,18 @@ def pair_phases(M, ctx, Xd, W0d, P, storage="f32"):
         M.mapi_pair_phases(ctx, True)  # the first run captured the graph: start again
         M.mapi_pca_topk(ctx, mat, K_COMP, "pair", "min1", ITERS, float(N), W0d, P_out=P)
         ph = M.mapi_pair_phases(ctx, False)
+        cl = M.mapi_pair_cluster_times(ctx)
     finally:
         M.mapi_matrix_free(ctx, mat)
-    return {k: round(v, 3) for k, v in ph.items()}
+    out = {k: round(v, 3) for k, v in ph.items()}
+    # how evenly the tile loop is spread: each streaming cluster's loop time
+    if cl:
+        srt = sorted(cl)
+        out["cluster_loop_us"] = {"clusters": len(cl), "min": round(srt[0], 2),
+                                  "median": round(srt[len(srt) // 2], 2),
+                                  "max": round(srt[-1], 2),
+                                  "by_cluster": [round(v, 1) for v in cl]}
+    return out
 
 
 def alu_probe(M, ctx) -> dict:

@@ -438,6 +438,15 @@ mapi_status mapi_get_stats(mapi_ctx* ctx, mapi_stats* out, int reset);
  * Not part of the method: it shows where a step's time goes. */
 mapi_status mapi_pair_phases(mapi_ctx* ctx, int enable, double* out_us);
 
+/* Each streaming cluster's loop time per pair step (from its CTAs' own
+ * start of the step to their arrival, averaged over its CTAs and the steps
+ * stamped since mapi_pair_phases last switched stamping on), in
+ * microseconds.  Synchronises ctx's stream.  *n <- the streaming clusters of
+ * the last pair launch (0 before any stamps); us[0 .. *n) is written when
+ * capacity >= *n, else MAPI_EINVAL.  A diagnostic of how evenly the tile
+ * loop's work and speed are spread over the clusters. */
+mapi_status mapi_pair_cluster_times(mapi_ctx* ctx, double* us, int capacity, int* n);
+
 /* Issue-rate probe of the MAVP term (the ALU roofline of the batched and
  * min-covariance kernels).  One full wave of blocks runs a register-resident
  * loop of independent chains; the slowest block's SM cycles (clock64) give

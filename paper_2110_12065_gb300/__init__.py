@@ -27,7 +27,7 @@ __all__ = [
     "mapi_autotune_batched", "mapi_submit", "mapi_poll", "mapi_cancel",
     "mapi_pagerank_sparse", "mapi_iterate_switch", "mapi_minibatch_momentum",
     "mapi_mavp_project", "mapi_image_reconstruct", "mapi_pair_phases", "mapi_debug_stall",
-    "mapi_rows_product", "mapi_pair_partial", "mapi_alu_probe",
+    "mapi_rows_product", "mapi_pair_partial", "mapi_alu_probe", "mapi_pair_cluster_times",
     "KERNEL_CLASSES",
     "OP", "ST", "FLAG_FINAL_L2", "FLAG_RAW_START", "SCALE_AUTO",
     "PCA_MINCOV", "PCA_PAIR", "STATUS",
@@ -122,6 +122,7 @@ def load(path: str | None = None):
         "mapi_pagerank_sparse": [p_, p_, p_, i, d, i, p_, i, d, p_, p_, p_],
         "mapi_profile": [p_, i],
         "mapi_pair_phases": [p_, i, p_],
+        "mapi_pair_cluster_times": [p_, p_, i, p_],
         "mapi_rows_product": [p_, p_, i, i, i, p_, p_],
         "mapi_alu_probe": [p_, i, p_],
         "mapi_pair_partial": [p_, p_, i, p_, p_],
@@ -472,6 +473,17 @@ def mapi_pair_phases(ctx, enable: bool = True) -> dict:
     out = (C.c_double * 8)()
     _check(load().mapi_pair_phases(ctx, 1 if enable else 0, out), "mapi_pair_phases", ctx)
     return {k: float(v) for k, v in zip(PAIR_PHASES, out)}
+
+
+def mapi_pair_cluster_times(ctx) -> list:
+    """Each streaming cluster's loop time per pair step (microseconds) over
+    the steps stamped since mapi_pair_phases last switched stamping on."""
+    cap = 128
+    us = (C.c_double * cap)()
+    n = C.c_int()
+    _check(load().mapi_pair_cluster_times(ctx, us, cap, C.byref(n)), "mapi_pair_cluster_times",
+           ctx)
+    return [float(us[c]) for c in range(n.value)]
 
 
 ALU_MIXES = ("min1_term_f32", "ffma", "fmnmx", "min1_term_bf16", "min1_term_bf16_x4")

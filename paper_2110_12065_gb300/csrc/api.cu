@@ -740,6 +740,22 @@ mapi_status mapi_pair_phases(mapi_ctx* ctx, int enable, double* out_us) {
   return MAPI_OK;
 }
 
+mapi_status mapi_pair_cluster_times(mapi_ctx* ctx, double* us, int capacity, int* n) {
+  if (!ctx || !n || capacity < 0 || (capacity > 0 && !us)) return MAPI_EINVAL;
+  DeviceGuard g(ctx->device);
+  MAPI_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  const int ns = std::min(ctx->pair_nstream, kPairPhaseClusters);
+  *n = ctx->pair_phases.p ? ns : 0;
+  if (!ctx->pair_phases.p) return MAPI_OK;
+  if (capacity < ns) return fail(ctx, MAPI_EINVAL, "capacity below the streaming clusters");
+  PairPhases h;
+  MAPI_CUDA_TRY(ctx, cudaMemcpy(&h, ctx->pair_phases.p, sizeof(h), cudaMemcpyDeviceToHost));
+  const double steps = (double)h.sum[7];
+  for (int c = 0; c < ns; ++c)
+    us[c] = steps > 0 ? (double)h.cl_ns[c] / (kPairClusterCtas * steps) / 1e3 : 0.0;
+  return MAPI_OK;
+}
+
 mapi_status mapi_debug_stall(mapi_ctx* ctx, int64_t limit_ns) {
   if (!ctx || limit_ns < 0 || limit_ns > 2000000000LL) return MAPI_EINVAL;
   ctx->stall_ns = (long long)limit_ns;

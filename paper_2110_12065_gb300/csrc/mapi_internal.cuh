@@ -112,9 +112,13 @@ namespace mapi {
 // the epilogue cluster sees it, [4] reduction of the accumulated row sums,
 // [5] deflation and its combination over the cluster, [6] norm,
 // normalisation, stop test and publication, [7] steps stamped.
+constexpr int kPairPhaseClusters = 128;  // streaming clusters the stamps cover at most
+constexpr int kPairClusterCtas = 4;      // CTAs per cluster of the pair solve
 struct PairPhases {
   unsigned long long start_min, loop_min, loop_max, prev_end;
   unsigned long long sum[8];
+  // per streaming cluster: its CTAs' loop times (own start to arrival), summed
+  unsigned long long cl_ns[kPairPhaseClusters];
 };
 }  // namespace mapi
 
@@ -153,6 +157,7 @@ struct mapi_ctx {
   bool phases_on = false;      // stamp the phases of pair steps
   DevBuf pair_phases;          // one mapi::PairPhases
   long long stall_ns = 0;      // > 0: fault-detection test of the bounded waits
+  int pair_nstream = 0;        // streaming clusters of the last pair launch
   int pair_coop = -1;          // cooperative cluster launch accepted (-1: not asked)
   // K1 may run in 8-CTA clusters on large matrices; off for
   // the serving loop, whose solves share the GPU with a persistent batched
@@ -307,6 +312,7 @@ struct DeflArgs {
 };
 struct PairPlan {
   const void* fn = nullptr;
+  const void* fn_stamp = nullptr;  // the variant with phase stamps (MIN1), or null
   int rw = 0;          // rows per warp (8, 16, 32)
   int clusters = 0;    // 4-CTA clusters of the launch, the epilogue's included
   int D_pad = 0;       // rows one cluster covers (4 x 8 x rw)

@@ -37,7 +37,7 @@ namespace cg = cooperative_groups;
 namespace mapi {
 namespace {
 
-constexpr int kPairWarps = 8, kPairCluster = 4, kPairStages = 3;
+constexpr int kPairWarps = 8, kPairCluster = kPairClusterCtas, kPairStages = 3;
 constexpr int kPairThreads = kPairWarps * 32;
 constexpr int kDeflMaxD = 1024;               // largest order of the pair mode
 constexpr int kDeflPadded = kDeflMaxD + kDeflMaxD / 8;
@@ -62,6 +62,8 @@ struct PairSolveArgs {
   int T;           // steps of this launch
   int dir0;        // walk direction of step 0 (alternates every step)
   int keep_tiles;  // a walk's last tiles are loaded to stay in L2
+  int nround;      // tiles every streaming cluster takes
+  int nfirst;      // clusters that take the remaining tiles (>= 1)
   int norm_l2;
   float denom;
   float* wb0;      // iterate of even steps (holds w_0 at the start)
@@ -223,7 +225,7 @@ __host__ __device__ constexpr int pair_epi_floats(int rc, int d_pad) {
 // the projection for DOT; CTA r's warp group g owns the earlier components
 // m = r + 4 g (mod 8)), w' = u / ||u||, the stop test, and the publication
 // of CTA r's rows of w' to the streaming CTAs of rank r.
-template <int RS, int OP>
+template <int RS, int OP, bool STAMP>
 __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster, float* fsh,
                               int s_exp) {
   constexpr int CS = kPairCluster;
@@ -299,7 +301,7 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
   __syncthreads();
   const float inv = ldexpf(1.f, -s_exp);
   const bool want_delta = a.ctl->tol > 0.f;
-  const bool stamp = a.phases && r == 0 && threadIdx.x == 0;
+  const bool stamp = STAMP && a.phases && r == 0 && threadIdx.x == 0;
 
   for (int t = 0; t < a.T; ++t) {
     // 1. every streaming CTA has added its row sums of step t
@@ -679,7 +681,9 @@ __device__ void pair_epilogue(const PairSolveArgs& a, cg::cluster_group& cluster
 }
 
 // ----------------------------------------------------------------- kernel
-template <int OP, int ST, int RW>
+// STAMP: the variant that takes the phase stamps (mapi_pair_phases); the
+// others carry no stamping code at all.
+template <int OP, int ST, int RW, bool STAMP>
 __global__ void __launch_bounds__(kPairThreads, 2)
     k_pair_solve(const __grid_constant__ CUtensorMap xmap, PairSolveArgs a) {
   using PC = PairCols<ST>;
@@ -708,6 +712,7 @@ __global__ void __launch_bounds__(kPairThreads, 2)
   __shared__ float tin[4][kPairCluster][TC];  // column partials pushed by each CTA
   __shared__ int s_err;
   __shared__ int s_stop;
+  __shared__ unsigned long long s_t0;  // phase stamps: this step's start
 
   if (threadIdx.x == 0) {
     s_err = 0;
@@ -734,13 +739,19 @@ __global__ void __launch_bounds__(kPairThreads, 2)
   const int s_exp = acc_scale_exp(__uint_as_float(*(volatile const unsigned*)&a.sync->xmax),
                                   a.ncols, a.D_pad, dot);
   if (cid == a.nstream) {
-    pair_epilogue<RC, OP>(a, cluster, reinterpret_cast<float*>(stage), s_exp);
+    pair_epilogue<RC, OP, STAMP>(a, cluster, reinterpret_cast<float*>(stage), s_exp);
     cluster.sync();  // peers may still read this CTA's shared memory until here
     return;
   }
 
   // ---- streaming cluster
-  const int nmine = a.ntiles > cid ? (a.ntiles - cid + a.nstream - 1) / a.nstream : 0;
+  // this cluster's tiles: nround rounds in which every streaming cluster
+  // takes one (tile cid + j nstream), then the rest in rounds over the first
+  // nfirst clusters only (their CTAs are placed first on their SMs and are
+  // issued ahead of the others, so they run faster)
+  const int extra = a.ntiles - a.nround * a.nstream;
+  const int nmine =
+      cid < a.nfirst ? a.nround + extra / a.nfirst + (cid < extra % a.nfirst ? 1 : 0) : a.nround;
   const unsigned total = (unsigned)a.T * (unsigned)nmine;  // tiles over all steps (< 2^31)
   const float scale = ldexpf(1.f, s_exp);
   const uint64_t pol_first = createpolicy_evict_first();
@@ -750,8 +761,9 @@ __global__ void __launch_bounds__(kPairThreads, 2)
     const unsigned g = issued++;
     const int s = (int)(g % kPairStages);
     const int t = (int)(g / nmine), j = (int)(g % nmine);
-    const int rev = (a.dir0 + t) & 1;
-    const int tile = cid + (rev ? nmine - 1 - j : j) * a.nstream;
+    const int jj = ((a.dir0 + t) & 1) ? nmine - 1 - j : j;
+    const int tile = jj < a.nround ? cid + jj * a.nstream
+                                   : a.nround * a.nstream + (jj - a.nround) * a.nfirst + cid;
     mbar_expect_tx(&full[s], kStageBytes);
     tma_load_2d_hint(stage + (size_t)s * RC * 32, &xmap, tile * TC, (int)crank * RC, &full[s],
                      j >= nmine - a.keep_tiles ? pol_last : pol_first);
@@ -863,7 +875,10 @@ __global__ void __launch_bounds__(kPairThreads, 2)
       }
       __syncthreads();
     }
-    if (a.phases && threadIdx.x == 0) atomicMin(&a.phases->start_min, gtimer_u64());
+    if (STAMP && a.phases && threadIdx.x == 0) {
+      s_t0 = gtimer_u64();
+      atomicMin(&a.phases->start_min, s_t0);
+    }
 #pragma unroll
     for (int j = 0; j < RW; ++j) acc[j] = 0.f;
     // two tiles in flight: A(j) overlaps the cluster exchange of tile j - 1
@@ -917,10 +932,11 @@ __global__ void __launch_bounds__(kPairThreads, 2)
     }
     if (threadIdx.x == 0) {
       if (s_err) atomicExch(&a.sync->err, 1);
-      if (a.phases) {
+      if (STAMP && a.phases) {
         const unsigned long long tn = gtimer_u64();
         atomicMin(&a.phases->loop_min, tn);
         atomicMax(&a.phases->loop_max, tn);
+        if (cid < kPairPhaseClusters) atomicAdd(&a.phases->cl_ns[cid], tn - s_t0);
       }
     }
     // arrival: this CTA's row sums are in (the release, cumulative over what
@@ -969,12 +985,12 @@ __global__ void k_pair_xmax(const void* __restrict__ X, int64_t elems, unsigned*
 
 __global__ void k_coop_probe() {}
 
-template <int OP, int ST>
+template <int OP, int ST, bool STAMP = false>
 const void* solve_fn(int rw) {
   switch (rw) {
-    case 8: return (const void*)k_pair_solve<OP, ST, 8>;
-    case 16: return (const void*)k_pair_solve<OP, ST, 16>;
-    case 32: return (const void*)k_pair_solve<OP, ST, 32>;
+    case 8: return (const void*)k_pair_solve<OP, ST, 8, STAMP>;
+    case 16: return (const void*)k_pair_solve<OP, ST, 16, STAMP>;
+    case 32: return (const void*)k_pair_solve<OP, ST, 32, STAMP>;
   }
   return nullptr;
 }
@@ -1028,13 +1044,17 @@ mapi_status plan_pair(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, PairPlan* pl
   const void* fn = nullptr;
   CUtensorMapDataType dt;
   int tc;
+  // the stamping variant exists for MIN1 (the benchmark's operator) only
+  pl->fn_stamp = nullptr;
   if (X->storage == MAPI_ST_F32) {
+    if (op == MAPI_OP_MIN1) pl->fn_stamp = solve_fn<MAPI_OP_MIN1, kF32, true>(rw);
     fn = op == MAPI_OP_MIN1 ? solve_fn<MAPI_OP_MIN1, kF32>(rw)
          : op == MAPI_OP_MIN2 ? solve_fn<MAPI_OP_MIN2, kF32>(rw)
                               : solve_fn<MAPI_OP_DOT, kF32>(rw);
     dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     tc = 32;
   } else if (X->storage == MAPI_ST_BF16) {
+    if (op == MAPI_OP_MIN1) pl->fn_stamp = solve_fn<MAPI_OP_MIN1, kBF16, true>(rw);
     fn = op == MAPI_OP_MIN1 ? solve_fn<MAPI_OP_MIN1, kBF16>(rw)
          : op == MAPI_OP_MIN2 ? solve_fn<MAPI_OP_MIN2, kBF16>(rw)
                               : solve_fn<MAPI_OP_DOT, kBF16>(rw);
@@ -1050,6 +1070,10 @@ mapi_status plan_pair(mapi_ctx* ctx, const mapi_mat* X, mapi_op op, PairPlan* pl
                       (size_t)pair_epi_floats(rc, d_pad) * sizeof(float));
   MAPI_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)pl->smem));
+  if (pl->fn_stamp)
+    MAPI_CUDA_TRY(ctx, cudaFuncSetAttribute(pl->fn_stamp,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)pl->smem));
   // the tensor map: X as [rows_pad][ld] with a (tc x rc) box; rows and
   // columns beyond the matrix read as zero
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
@@ -1125,7 +1149,16 @@ mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
   if (T <= 0) return MAPI_OK;
   const int TCc = (X->storage == MAPI_ST_F32) ? 32 : 64;
   const int64_t ntiles = (X->ld + TCc - 1) / TCc;
-  const int64_t nmine_max = (ntiles + pl.clusters - 2) / (pl.clusters - 1);
+  // the tile split: a share of the tiles goes to the first half of the
+  // streaming clusters only
+  const int nstream = pl.clusters - 1;
+  const int nfirst = std::max(1, nstream / 2);
+  // (measured on GB300: the best share for FP32 X, whose loop is bound by
+  // HBM, is 6 % of the tiles; for BF16, bound by issue, 26 %)
+  const double skew = X->storage == MAPI_ST_BF16 ? 0.26 : 0.06;
+  const int64_t nround = (int64_t)((double)ntiles * (1.0 - skew)) / nstream;
+  const int64_t rest = ntiles - nround * nstream;
+  const int64_t nmine_max = nround + (rest + nfirst - 1) / nfirst;
   if ((int64_t)T * nmine_max >= (1ll << 31))
     return fail(ctx, MAPI_EINVAL, "pair mode: max_iters x column tiles per cluster >= 2^31");
   const size_t acc_bytes = sizeof(unsigned long long) * (2 * kAccCopies + 1) * (size_t)pl.D_pad;
@@ -1143,6 +1176,8 @@ mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
   a.T = T;
   a.dir0 = dir0 & 1;
   a.keep_tiles = pair_keep_tiles(ctx, X, pl);
+  a.nround = (int)nround;
+  a.nfirst = nfirst;
   a.norm_l2 = norm_l2;
   a.denom = denom;
   a.wb0 = wb0;
@@ -1152,7 +1187,9 @@ mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
   a.ctl = ctl;
   a.defl = defl;
   a.stall_ns = ctx->stall_ns;
-  a.phases = ctx->phases_on ? (PairPhases*)ctx->pair_phases.p : nullptr;
+  const bool stamped = ctx->phases_on && ctx->pair_phases.p && pl.fn_stamp;
+  a.phases = stamped ? (PairPhases*)ctx->pair_phases.p : nullptr;
+  ctx->pair_nstream = a.nstream;
   a.raw_out = raw_out;
   a.wpub = reinterpret_cast<unsigned long long*>(scratch) + 2 * kAccCopies * (size_t)pl.D_pad;
   cudaLaunchConfig_t cfg = {};
@@ -1171,7 +1208,7 @@ mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
   cfg.numAttrs = pl.coop ? 2 : 1;
   void* args[] = {(void*)&pl.map, &a};
   cudaEvent_t ev = prof_begin(ctx, s);
-  MAPI_CUDA_TRY(ctx, cudaLaunchKernelExC(&cfg, pl.fn, args));
+  MAPI_CUDA_TRY(ctx, cudaLaunchKernelExC(&cfg, stamped ? pl.fn_stamp : pl.fn, args));
   prof_end(ctx, s, ev, MAPI_KC_PAIR, (double)T * X->rows * X->cols * elem_bytes(X->storage),
            2.0 * T * X->rows * X->cols, T);
   count_launch(ctx);

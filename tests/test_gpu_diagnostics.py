@@ -1,6 +1,7 @@
 """The diagnostic entry points: the ALU roofline probe returns rates that
-the hardware allows, and the pair step's phase stamps count the steps that
-ran and give non-negative phase times."""
+the hardware allows, the pair step's phase stamps count the steps that ran
+and give non-negative phase times and per-cluster loop times, and the
+stamping kernel gives the same bits as the plain one."""
 import math
 
 import numpy as np
@@ -43,5 +44,27 @@ def test_pair_phase_stamps_count_the_steps(mapi_ctx):
     for name, v in ph.items():
         assert math.isfinite(v) and v >= 0.0, (name, v)
     assert ph["start_to_last_arrival"] >= ph["start_to_first_arrival"]
+    # each streaming cluster's loop time lies within the step's loop
+    cl = M.mapi_pair_cluster_times(mapi_ctx)
+    assert len(cl) >= 1
+    assert all(0.0 < v <= ph["start_to_last_arrival"] + 1.0 for v in cl), (cl, ph)
     # stamping off: nothing more is counted
     assert M.mapi_pair_phases(mapi_ctx, False)["steps"] == k * T
+
+
+@pytest.mark.parametrize("st", ["f32", "bf16"])
+def test_stamped_solve_gives_the_same_bits(mapi_ctx, st):
+    # the stamping kernel is a separate instantiation of the same arithmetic
+    D, N, k, T = 300, 20000, 3, 12
+    X = datagen.spiked_pca_data(D, N, seed=82)
+    W0 = to_dev(np.stack([datagen.start_vector(D, seed=820 + c) for c in range(k)]))
+    mat = M.mapi_matrix_upload(mapi_ctx, to_dev(X), st)
+    try:
+        P0, it0 = M.mapi_pca_topk(mapi_ctx, mat, k, "pair", "min1", T, float(N), W0)
+        M.mapi_pair_phases(mapi_ctx, True)
+        P1, it1 = M.mapi_pca_topk(mapi_ctx, mat, k, "pair", "min1", T, float(N), W0)
+        assert M.mapi_pair_phases(mapi_ctx, False)["steps"] == k * T
+    finally:
+        M.mapi_matrix_free(mapi_ctx, mat)
+    assert list(it0) == list(it1)
+    np.testing.assert_array_equal(P0.cpu().numpy(), P1.cpu().numpy())
