@@ -61,7 +61,6 @@ struct PairSolveArgs {
   int nstream;     // streaming clusters (the epilogue cluster comes after them)
   int T;           // steps of this launch
   int dir0;        // walk direction of step 0 (alternates every step)
-  int keep_tiles;  // a walk's last tiles are loaded to stay in L2
   int nround;      // tiles every streaming cluster takes
   int nfirst;      // clusters that take the remaining tiles (>= 1)
   int norm_l2;
@@ -754,8 +753,10 @@ __global__ void __launch_bounds__(kPairThreads, 2)
       cid < a.nfirst ? a.nround + extra / a.nfirst + (cid < extra % a.nfirst ? 1 : 0) : a.nround;
   const unsigned total = (unsigned)a.T * (unsigned)nmine;  // tiles over all steps (< 2^31)
   const float scale = ldexpf(1.f, s_exp);
+  // every tile is read once per step with the evict-first policy (the walk
+  // reversal still finds the last tiles of a step in L2 at the start of the
+  // next); marking a share of them evict-last measured slower
   const uint64_t pol_first = createpolicy_evict_first();
-  const uint64_t pol_last = createpolicy_evict_last();
   unsigned issued = 0;  // thread 0: tiles issued (global order over the steps)
   auto issue_next = [&]() {
     const unsigned g = issued++;
@@ -766,7 +767,7 @@ __global__ void __launch_bounds__(kPairThreads, 2)
                                    : a.nround * a.nstream + (jj - a.nround) * a.nfirst + cid;
     mbar_expect_tx(&full[s], kStageBytes);
     tma_load_2d_hint(stage + (size_t)s * RC * 32, &xmap, tile * TC, (int)crank * RC, &full[s],
-                     j >= nmine - a.keep_tiles ? pol_last : pol_first);
+                     pol_first);
   };
   if (threadIdx.x == 0)
     while (issued < total && issued < kPairStages) issue_next();
@@ -1133,15 +1134,6 @@ mapi_status launch_pair_prepare(mapi_ctx* ctx, cudaStream_t s, const PairPlan& p
   return MAPI_OK;
 }
 
-// Keep the tiles a walk reads last in L2 for the next step (which walks the
-// other way): together about 60 % of L2.
-static int pair_keep_tiles(const mapi_ctx* ctx, const mapi_mat* X, const PairPlan& pl) {
-  const int TC = (X->storage == MAPI_ST_F32) ? 32 : 64;
-  const double tile_bytes = (double)kPairCluster * kPairWarps * pl.rw * TC * elem_bytes(X->storage);
-  const double keep = 0.6 * ctx->l2_bytes / (tile_bytes * (pl.clusters - 1));
-  return keep < 0 ? 0 : (int)keep;
-}
-
 mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
                               const mapi_mat* X, void* scratch, float* wb0, float* wb1,
                               const DeflArgs& defl, IterCtl* ctl, int T, int norm_l2,
@@ -1175,7 +1167,6 @@ mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
   a.nstream = pl.clusters - 1;
   a.T = T;
   a.dir0 = dir0 & 1;
-  a.keep_tiles = pair_keep_tiles(ctx, X, pl);
   a.nround = (int)nround;
   a.nfirst = nfirst;
   a.norm_l2 = norm_l2;
