@@ -1146,8 +1146,8 @@ mapi_status launch_pair_solve(mapi_ctx* ctx, cudaStream_t s, const PairPlan& pl,
   const int nstream = pl.clusters - 1;
   const int nfirst = std::max(1, nstream / 2);
   // (measured on GB300: the best share for FP32 X, whose loop is bound by
-  // HBM, is 6 % of the tiles; for BF16, bound by issue, 26 %)
-  const double skew = X->storage == MAPI_ST_BF16 ? 0.26 : 0.06;
+  // HBM, is 3 % of the tiles; for BF16, bound by issue, 26 %)
+  const double skew = X->storage == MAPI_ST_BF16 ? 0.26 : 0.03;
   const int64_t nround = (int64_t)((double)ntiles * (1.0 - skew)) / nstream;
   const int64_t rest = ntiles - nround * nstream;
   const int64_t nmine_max = nround + (rest + nfirst - 1) / nfirst;
