@@ -231,7 +231,24 @@ struct Chunk<kI16> {
     const uint32_t wd = (&raw.x)[e >> 1];
     return (e & 1) ? ((int)wd >> 16) : ((int)(wd << 16) >> 16);
   }
+  // word k: elements 2k (low half) and 2k + 1 (high half)
+  __device__ __forceinline__ uint32_t raw_word(int k) const { return (&raw.x)[k]; }
 };
+
+// acc + s0 clamp(a0, lo0, hi0) + s1 clamp(a1, lo1, hi1) for two int16
+// columns packed in a word (element 0 in the low half): packed signed 16-bit
+// max and min, then a two-way dot product of the clamped pair with the
+// signs s0, s1 (+-1, the low two bytes of sg), accumulated in INT32.  Every
+// operation is exact.
+__device__ __forceinline__ int i16x2_clamp_dot(uint32_t a2, uint32_t lo2, uint32_t hi2,
+                                               uint32_t sg, int acc) {
+  uint32_t c;
+  asm("max.s16x2 %0, %1, %2;" : "=r"(c) : "r"(a2), "r"(lo2));
+  asm("min.s16x2 %0, %0, %1;" : "+r"(c) : "r"(hi2));
+  int d;
+  asm("dp2a.lo.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(c), "r"(sg), "r"(acc));
+  return d;
+}
 
 template <>
 struct Chunk<kI8> {

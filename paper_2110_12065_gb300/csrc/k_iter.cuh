@@ -509,30 +509,73 @@ __global__ void __launch_bounds__(WARPS * 32)
     for (int v = 0; v < V; ++v) acc[r][v] = 0;
   const uint8_t* arow = g.A + (int64_t)row0 * g.row_bytes;
   const int* w = reinterpret_cast<const int*>(g.w);
-  for (int c = c_beg + lane; c < c_end; c += 32) {
-    Ch x[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) x[r].raw = ld_stream(arow + r * g.row_bytes + (int64_t)c * 16);
+  // int16 MIN1 / MIN2: two columns per 32-bit word at once, clamped with
+  // packed 16-bit min/max (exact: the bounds are the iterate's entries
+  // limited to +-32767, which changes no min against a stored int16) and
+  // added with their signs by one two-way dot product into the INT32 sum
+  constexpr bool kPacked = ST == kI16 && (OP == MAPI_OP_MIN1 || OP == MAPI_OP_MIN2);
+  auto consume = [&](const Ch (&x)[R], int c) {
 #pragma unroll
     for (int grp = 0; grp < E / 4; ++grp) {
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         const int4 wv = __ldg(reinterpret_cast<const int4*>(w + (int64_t)v * g.wst + (int64_t)c * E + grp * 4));
-        const auto p0 = IOp<OP>::prep(wv.x);
-        const auto p1 = IOp<OP>::prep(wv.y);
-        const auto p2 = IOp<OP>::prep(wv.z);
-        const auto p3 = IOp<OP>::prep(wv.w);
+        if constexpr (kPacked) {
+          uint32_t lo2[2], hi2[2], sg[2];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          int s = acc[r][v];
-          s = IOp<OP>::term(x[r].get(grp * 4 + 0), p0, s);
-          s = IOp<OP>::term(x[r].get(grp * 4 + 1), p1, s);
-          s = IOp<OP>::term(x[r].get(grp * 4 + 2), p2, s);
-          s = IOp<OP>::term(x[r].get(grp * 4 + 3), p3, s);
-          acc[r][v] = s;
+          for (int h = 0; h < 2; ++h) {
+            const int w0 = h ? wv.z : wv.x, w1 = h ? wv.w : wv.y;
+            const auto p0 = IOp<OP>::prep(w0);
+            const auto p1 = IOp<OP>::prep(w1);
+            const int l0 = max(p0.lo, -32767), h0 = min(p0.hi, 32767);
+            const int l1 = max(p1.lo, -32767), h1 = min(p1.hi, 32767);
+            lo2[h] = ((uint32_t)l0 & 0xFFFFu) | ((uint32_t)l1 << 16);
+            hi2[h] = ((uint32_t)h0 & 0xFFFFu) | ((uint32_t)h1 << 16);
+            sg[h] = ((uint32_t)p0.s & 0xFFu) | (((uint32_t)p1.s & 0xFFu) << 8);
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            int s = acc[r][v];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              s = i16x2_clamp_dot(x[r].raw_word(grp * 2 + h), lo2[h], hi2[h], sg[h], s);
+            acc[r][v] = s;
+          }
+        } else {
+          const auto p0 = IOp<OP>::prep(wv.x);
+          const auto p1 = IOp<OP>::prep(wv.y);
+          const auto p2 = IOp<OP>::prep(wv.z);
+          const auto p3 = IOp<OP>::prep(wv.w);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            int s = acc[r][v];
+            s = IOp<OP>::term(x[r].get(grp * 4 + 0), p0, s);
+            s = IOp<OP>::term(x[r].get(grp * 4 + 1), p1, s);
+            s = IOp<OP>::term(x[r].get(grp * 4 + 2), p2, s);
+            s = IOp<OP>::term(x[r].get(grp * 4 + 3), p3, s);
+            acc[r][v] = s;
+          }
         }
       }
     }
+  };
+  int c = c_beg + lane;
+  // two chunks per row in flight per lane
+  for (; c + 32 < c_end; c += 64) {
+    Ch x[R], z[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      x[r].raw = ld_stream(arow + r * g.row_bytes + (int64_t)c * 16);
+      z[r].raw = ld_stream(arow + r * g.row_bytes + (int64_t)(c + 32) * 16);
+    }
+    consume(x, c);
+    consume(z, c + 32);
+  }
+  if (c < c_end) {
+    Ch x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r].raw = ld_stream(arow + r * g.row_bytes + (int64_t)c * 16);
+    consume(x, c);
   }
 #pragma unroll
   for (int r = 0; r < R; ++r)
