@@ -15,7 +15,7 @@ def declared_symbols():
     return sorted(set(re.findall(r"\b(mapi_[a-z0-9_]+)\s*\(", text)))
 
 
-def test_header_declares_the_survey_entry_points():
+def test_header_declares_the_core_entry_points():
     syms = declared_symbols()
     for name in ("mapi_create", "mapi_destroy", "mapi_iterate", "mapi_pca_topk",
                  "mapi_pagerank", "mapi_matrix_upload", "mapi_status_str"):
