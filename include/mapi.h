@@ -135,6 +135,10 @@ const char* mapi_last_error(const mapi_ctx* ctx);
  * float storages.  The packed copy pads every row to a multiple of 16 bytes
  * (and the row count to a multiple of 64) with zeros; zero entries add
  * nothing to any product.
+ * A host source is copied into a device staging buffer that the context
+ * keeps (grown to the largest host upload so far, released by
+ * mapi_destroy); the call returns once the copy is done, so the host buffer
+ * may then be reused.
  * Errors: MAPI_EINVAL (sizes, ld < cols, storage, q out of [0, 24] or
  * entries too large for the integer range), MAPI_ENONFINITE (NaN/Inf
  * entry), MAPI_ENOMEM, MAPI_ECUDA.
@@ -144,7 +148,10 @@ mapi_status mapi_matrix_upload(mapi_ctx* ctx, const void* src, int src_is_device
                                mapi_storage storage, int int_scale_log2,
                                mapi_mat** out);
 
-/* Free a packed matrix (synchronises the context's stream first). */
+/* Free a packed matrix (synchronises the context's stream first).  The
+ * device storage of up to two freed matrices is kept by the context and
+ * reused by the next matrix of exactly the same size; mapi_destroy, or an
+ * allocation that would otherwise fail, releases it. */
 mapi_status mapi_matrix_free(mapi_ctx* ctx, mapi_mat* m);
 
 /* Shape and storage of a packed matrix; any output pointer may be NULL.

@@ -176,6 +176,13 @@ struct DeviceGuard {
 
 namespace mapi {
 
+void release_matrix_pool(mapi_ctx* ctx) {
+  if (ctx->mat_pool.empty()) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& b : ctx->mat_pool) cudaFree(b.first);
+  ctx->mat_pool.clear();
+}
+
 mapi_status free_matrix(mapi_ctx* ctx, mapi_mat* m) {
   // graphs captured for this matrix can never be replayed again
   for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
@@ -186,7 +193,15 @@ mapi_status free_matrix(mapi_ctx* ctx, mapi_mat* m) {
       ++it;
     }
   }
-  if (m->data) cudaFree(m->data);
+  if (m->data) {
+    // kept for the next matrix of this size (a repeated upload of the same
+    // shape then needs neither cudaMalloc nor the synchronising cudaFree)
+    if (ctx->pool_matrices && (int)ctx->mat_pool.size() < kMatPoolBlocks) {
+      ctx->mat_pool.emplace_back(m->data, m->bytes);
+    } else {
+      cudaFree(m->data);
+    }
+  }
   if (m->row_scale) cudaFree(m->row_scale);
   if (m->row_exp) cudaFree(m->row_exp);
   ctx->mats.erase(m);
@@ -205,10 +220,22 @@ mapi_status alloc_matrix(mapi_ctx* ctx, int rows, int cols, mapi_storage st,
   m->ld = ((int64_t)cols * eb + 15) / 16 * 16 / eb;
   m->storage = st;
   m->bytes = (size_t)m->rows_pad * m->ld * eb;
-  if (cudaMalloc(&m->data, m->bytes) != cudaSuccess) {
+  for (size_t i = 0; i < ctx->mat_pool.size(); ++i)
+    if (ctx->mat_pool[i].second == m->bytes) {
+      m->data = ctx->mat_pool[i].first;
+      ctx->mat_pool.erase(ctx->mat_pool.begin() + i);
+      break;
+    }
+  if (!m->data && cudaMalloc(&m->data, m->bytes) != cudaSuccess) {
     cudaGetLastError();
-    delete m;
-    return fail(ctx, MAPI_ENOMEM, "matrix allocation failed");
+    // the kept blocks first go back to the device, then one more try
+    release_matrix_pool(ctx);
+    if (cudaMalloc(&m->data, m->bytes) != cudaSuccess) {
+      cudaGetLastError();
+      m->data = nullptr;
+      delete m;
+      return fail(ctx, MAPI_ENOMEM, "matrix allocation failed");
+    }
   }
   if (st == MAPI_ST_FP8E4M3_ROWPOW2) {
     if (cudaMalloc(&m->row_scale, sizeof(float) * m->rows_pad) != cudaSuccess ||
@@ -384,9 +411,10 @@ mapi_status mapi_destroy(mapi_ctx* ctx) {
   prof_collect(ctx, ctx->pending, true);
   std::set<mapi_mat*> ms = ctx->mats;
   for (auto* m : ms) free_matrix(ctx, m);
+  release_matrix_pool(ctx);
   for (DevBuf* b : {&ctx->ypart, &ctx->wbuf0, &ctx->wbuf1, &ctx->ctl, &ctx->aux, &ctx->mcpart,
                     &ctx->pca_c0, &ctx->pca_c1, &ctx->pca_q, &ctx->pca_defl, &ctx->batch,
-                    &ctx->hyb, &ctx->outer, &ctx->img, &ctx->pair_phases})
+                    &ctx->hyb, &ctx->outer, &ctx->img, &ctx->pair_phases, &ctx->upload_staging})
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
@@ -409,28 +437,33 @@ mapi_status mapi_matrix_upload(mapi_ctx* ctx, const void* src, int src_is_device
   DeviceGuard g(ctx->device);
   const float* dsrc = (const float*)src;
   int64_t dld = ld;
-  DevBuf staging;
   if (!src_is_device) {
-    size_t bytes = (size_t)rows * cols * sizeof(float);
-    if (cudaMalloc(&staging.p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ctx, MAPI_ENOMEM, "staging allocation failed");
+    // the context's staging buffer (grown here without touching the graphs,
+    // which never refer to it)
+    const size_t bytes = (size_t)rows * cols * sizeof(float);
+    DevBuf& sb = ctx->upload_staging;
+    if (sb.bytes < bytes) {
+      cudaStreamSynchronize(ctx->stream);
+      if (sb.p) cudaFree(sb.p);
+      sb.p = nullptr;
+      sb.bytes = 0;
+      if (cudaMalloc(&sb.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        sb.p = nullptr;
+        return fail(ctx, MAPI_ENOMEM, "staging allocation failed");
+      }
+      sb.bytes = bytes;
     }
-    cudaError_t e = cudaMemcpy2DAsync(staging.p, cols * sizeof(float), src, ld * sizeof(float),
+    cudaError_t e = cudaMemcpy2DAsync(sb.p, cols * sizeof(float), src, ld * sizeof(float),
                                       cols * sizeof(float), rows, cudaMemcpyHostToDevice,
                                       ctx->stream);
-    if (e != cudaSuccess) {
-      cudaFree(staging.p);
-      return cuda_fail(ctx, e, "cudaMemcpy2DAsync");
-    }
-    dsrc = (const float*)staging.p;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy2DAsync");
+    dsrc = (const float*)sb.p;
     dld = cols;
   }
   mapi_status s = pack_from_device(ctx, dsrc, rows, cols, dld, storage, int_scale_log2, out);
-  if (staging.p) {
-    cudaStreamSynchronize(ctx->stream);
-    cudaFree(staging.p);
-  }
+  // the caller may reuse its host buffer once this returns
+  if (!src_is_device) cudaStreamSynchronize(ctx->stream);
   return s;
 }
 

@@ -122,6 +122,7 @@ struct PairPhases {
 };
 }  // namespace mapi
 
+constexpr int kMatPoolBlocks = 2;
 struct mapi_ctx {
   int device = 0;
   int sm_count = 0;
@@ -156,6 +157,13 @@ struct mapi_ctx {
   bool prof_on = false;
   bool phases_on = false;      // stamp the phases of pair steps
   DevBuf pair_phases;          // one mapi::PairPhases
+  // Host uploads are copied into this staging buffer (grown to the largest
+  // upload, kept until mapi_destroy) before they are packed.
+  DevBuf upload_staging;
+  // Device storage of freed matrices kept for the next matrix of the same
+  // size (at most kMatPoolBlocks blocks; off where memory is budgeted).
+  std::vector<std::pair<void*, size_t>> mat_pool;
+  bool pool_matrices = true;
   long long stall_ns = 0;      // > 0: fault-detection test of the bounded waits
   int pair_nstream = 0;        // streaming clusters of the last pair launch
   int pair_coop = -1;          // cooperative cluster launch accepted (-1: not asked)
@@ -211,6 +219,7 @@ mapi_status launch_cached_graph(mapi_ctx* ctx, const std::vector<int64_t>& key,
 void finish_graph(mapi_ctx* ctx, GraphEntry* g);
 
 // Grow a scratch buffer (drops cached graphs when an address changes).
+void release_matrix_pool(mapi_ctx* ctx);
 mapi_status ensure(mapi_ctx* ctx, DevBuf& b, size_t bytes);
 
 // Packed matrices owned by the context (api.cu): an uninitialised rows x cols

@@ -605,6 +605,9 @@ mapi_status ensure_server(mapi_ctx* ctx, Server** out) {
       return s;
     }
     sv->child->gemv_clusters = false;
+    // the served matrices live within the admission budget: no kept blocks
+    sv->child->pool_matrices = false;
+    sv->bchild->pool_matrices = false;
     {
       int prev = 0;
       cudaGetDevice(&prev);
