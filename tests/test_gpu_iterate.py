@@ -399,3 +399,38 @@ def test_switch_reports_a_failed_first_phase(mapi_ctx):
         assert e.value.partial[1][1] == 0
     finally:
         M.mapi_matrix_free(mapi_ctx, mat)
+
+
+def test_reused_storage_and_staging_hold_no_stale_data(mapi_ctx):
+    # The context keeps the storage of freed matrices for the next matrix of
+    # the same size, and one staging buffer for host uploads (grown to the
+    # largest): a solve on a matrix that lands in reused storage, or that
+    # came through a staging buffer last filled by a larger upload, must
+    # equal the solve on a fresh upload in a fresh context.
+    n, T = 300, 8
+    w0 = to_dev(datagen.start_vector(n, seed=91))
+    mats = [datagen.symmetric_gaussian(n, seed=90 + k).astype(np.float32) for k in range(2)]
+    big = datagen.symmetric_gaussian(2 * n, seed=95).astype(np.float32)
+
+    w0_big = to_dev(datagen.start_vector(2 * n, seed=96))
+
+    def solve(ctx, A, host):
+        mat = M.mapi_matrix_upload(ctx, A if host else to_dev(A), "f32")
+        try:
+            w, _, _ = M.mapi_iterate(ctx, mat, "min1", w0 if A.shape[0] == n else w0_big, T)
+            return to_host(w)
+        finally:
+            M.mapi_matrix_free(ctx, mat)
+
+    fresh = M.mapi_create(0)
+    try:
+        want = [solve(fresh, A, host=False) for A in mats]
+    finally:
+        M.mapi_destroy(fresh)
+    got = []
+    for k in (0, 1, 0, 1):
+        got.append(solve(mapi_ctx, mats[k], host=(k == 1)))
+        # a larger host upload in between grows the staging buffer
+        solve(mapi_ctx, big, host=True)
+    for g, k in zip(got, (0, 1, 0, 1)):
+        np.testing.assert_array_equal(g, want[k])
