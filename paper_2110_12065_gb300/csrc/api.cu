@@ -454,10 +454,13 @@ mapi_status mapi_matrix_upload(mapi_ctx* ctx, const void* src, int src_is_device
       }
       sb.bytes = bytes;
     }
-    cudaError_t e = cudaMemcpy2DAsync(sb.p, cols * sizeof(float), src, ld * sizeof(float),
-                                      cols * sizeof(float), rows, cudaMemcpyHostToDevice,
-                                      ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy2DAsync");
+    // one flat copy when the rows are contiguous, else a pitched one
+    cudaError_t e =
+        ld == cols
+            ? cudaMemcpyAsync(sb.p, src, bytes, cudaMemcpyHostToDevice, ctx->stream)
+            : cudaMemcpy2DAsync(sb.p, cols * sizeof(float), src, ld * sizeof(float),
+                                cols * sizeof(float), rows, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "host to device copy");
     dsrc = (const float*)sb.p;
     dld = cols;
   }
