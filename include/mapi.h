@@ -519,6 +519,16 @@ mapi_status mapi_iterate_batched(mapi_ctx* ctx, const mapi_batch_item* items, in
 mapi_status mapi_autotune_batched(mapi_ctx* ctx, const mapi_batch_item* items, int count,
                                   mapi_op op, int nvec, int iters, int* chosen);
 
+/*
+ * Set the batched solve's rows per warp (1, 2, 4 or 8) for this context,
+ * storage (MAPI_ST_F32 or MAPI_ST_BF16) and vector count, as the autotuner
+ * would: a way to pin a tuning found earlier, or to run a chosen variant.
+ * The results of a solve agree within FP32 rounding whatever the value (the
+ * order of the additions differs).  MAPI_EINVAL for other values.
+ */
+mapi_status mapi_set_batched_rows(mapi_ctx* ctx, mapi_storage storage, int nvec,
+                                  int rows_per_warp);
+
 /* ------------------------------------------------------------------ */
 /* Serving: PCA and PageRank requests admitted as they arrive.          */
 /* ------------------------------------------------------------------ */

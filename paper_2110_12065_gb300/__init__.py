@@ -28,6 +28,7 @@ __all__ = [
     "mapi_pagerank_sparse", "mapi_iterate_switch", "mapi_minibatch_momentum",
     "mapi_mavp_project", "mapi_image_reconstruct", "mapi_pair_phases", "mapi_debug_stall",
     "mapi_rows_product", "mapi_pair_partial", "mapi_alu_probe", "mapi_pair_cluster_times",
+    "mapi_set_batched_rows",
     "KERNEL_CLASSES",
     "OP", "ST", "FLAG_FINAL_L2", "FLAG_RAW_START", "SCALE_AUTO",
     "PCA_MINCOV", "PCA_PAIR", "STATUS",
@@ -123,6 +124,7 @@ def load(path: str | None = None):
         "mapi_profile": [p_, i],
         "mapi_pair_phases": [p_, i, p_],
         "mapi_pair_cluster_times": [p_, p_, i, p_],
+        "mapi_set_batched_rows": [p_, i, i, i],
         "mapi_rows_product": [p_, p_, i, i, i, p_, p_],
         "mapi_alu_probe": [p_, i, p_],
         "mapi_pair_partial": [p_, p_, i, p_, p_],
@@ -597,6 +599,14 @@ def mapi_autotune_batched(ctx, items, op, nvec: int, iters: int = 2) -> int:
     _check(load().mapi_autotune_batched(ctx, arr, len(items), opi, int(nvec), int(iters),
                                         C.byref(ch)), "mapi_autotune_batched", ctx)
     return ch.value
+
+
+def mapi_set_batched_rows(ctx, storage, nvec: int, rows_per_warp: int) -> None:
+    """Pin the batched solve's rows per warp (1, 2, 4, 8) for this context,
+    storage ("f32" / "bf16") and vector count, as the autotuner would."""
+    st = ST[storage] if isinstance(storage, str) else int(storage)
+    _check(load().mapi_set_batched_rows(ctx, st, int(nvec), int(rows_per_warp)),
+           "mapi_set_batched_rows", ctx)
 
 
 # host arrays of each open request (the library reads and writes them until

@@ -672,6 +672,19 @@ extern "C" mapi_status mapi_iterate_batched(mapi_ctx* ctx, const mapi_batch_item
   return result;
 }
 
+extern "C" mapi_status mapi_set_batched_rows(mapi_ctx* ctx, mapi_storage storage, int nvec,
+                                             int rows_per_warp) {
+  if (!ctx) return MAPI_EINVAL;
+  if (storage != MAPI_ST_F32 && storage != MAPI_ST_BF16)
+    return fail(ctx, MAPI_EINVAL, "batched rows: F32 or BF16 storage");
+  if (nvec < 1 || nvec > 8) return fail(ctx, MAPI_EINVAL, "batched rows: nvec in [1, 8]");
+  if (rows_per_warp != 1 && rows_per_warp != 2 && rows_per_warp != 4 && rows_per_warp != 8)
+    return fail(ctx, MAPI_EINVAL, "batched rows: 1, 2, 4 or 8");
+  const int V = pow2v(nvec);
+  ctx->batch_rows_per_warp[storage == MAPI_ST_F32 ? 0 : 1][V == 1 ? 0 : 1] = rows_per_warp;
+  return MAPI_OK;
+}
+
 extern "C" mapi_status mapi_autotune_batched(mapi_ctx* ctx, const mapi_batch_item* items,
                                              int count, mapi_op op, int nvec, int iters,
                                              int* chosen) {

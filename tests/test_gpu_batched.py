@@ -134,3 +134,35 @@ def test_batched_full_size_sampled(mapi_ctx):
     finally:
         for m in mats:
             M.mapi_matrix_free(mapi_ctx, m)
+
+
+@pytest.mark.parametrize("st", ["f32", "bf16"])
+@pytest.mark.parametrize("nvec", [1, 4])
+@pytest.mark.parametrize("rows", [1, 2, 4, 8])
+def test_batched_every_rows_per_warp_variant(mapi_ctx, st, nvec, rows):
+    # each kernel variant the autotuner may pick (eight BF16 rows per warp
+    # read half chunks), forced through mapi_set_batched_rows, against the
+    # FP64 oracle on large (cluster) and small (one CTA) instances
+    mats, items, hostA, W0s = make_batch(mapi_ctx, st, nvec, seed0=40)
+    try:
+        M.mapi_set_batched_rows(mapi_ctx, st, nvec, rows)
+        it, dl, sts = M.mapi_iterate_batched(mapi_ctx, items, "min1", nvec, 10)
+        for k, ((mat, w0, w_out), A, W0) in enumerate(zip(items, hostA, W0s)):
+            Ad = A.astype(np.float64) if st == "f32" else oracle.quant_bf16(A)
+            got = to_host(w_out)
+            for v in range(nvec):
+                ost, want, oit, _ = oracle.mapi("min1", Ad, W0[v].astype(np.float64), 10)
+                assert sts[k, v] == ost and it[k, v] == oit
+                assert rel_l1(got[v], want) <= TOL32, (st, nvec, rows, SIZES[k], v)
+    finally:
+        M.mapi_set_batched_rows(mapi_ctx, st, nvec, 2)
+        for m in mats:
+            M.mapi_matrix_free(mapi_ctx, m)
+
+
+def test_set_batched_rows_rejects_other_values(mapi_ctx):
+    for bad in (0, 3, 16):
+        with pytest.raises(M.MapiError):
+            M.mapi_set_batched_rows(mapi_ctx, "f32", 4, bad)
+    with pytest.raises(M.MapiError):
+        M.mapi_set_batched_rows(mapi_ctx, "fp8", 4, 2)
