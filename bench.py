@@ -321,7 +321,9 @@ def batched_leg(M, ctx, torch, dev, probe, hbm, stg, n_inst=4096, steps=100):
 def pair_phases(M, ctx, Xd, W0d, P, storage="f32"):
     """Where the time of a pair step goes: the headline solve run once with
     the kernel's %globaltimer phase stamps on (microseconds per step,
-    averaged over its 800 steps).  The stamps add a few atomics per CTA."""
+    averaged over its 800 steps), and each streaming cluster's loop time.  The
+    stamps run in a separate instantiation of the kernel and cost about 1 us
+    per step themselves."""
     mat = M.mapi_matrix_upload(ctx, Xd, storage)
     try:
         M.mapi_pair_phases(ctx, True)
